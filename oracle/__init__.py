@@ -1,0 +1,179 @@
+"""FP64 CPU oracle for FDK and FDK-OD -- test infrastructure only.
+
+Only the test-suite, the smoke check and the benchmark's CPU-baseline leg use
+this package.  It shares no code with the CUDA library: the arithmetic lives
+in ``oracle.c`` (plain C, FP64, OpenMP over independent outputs, compiled
+with -ffp-contract=off), and this module only marshals numpy arrays.
+
+Functions and the passages they follow:
+  filter / filter_rows   cosine weight + Ram-Lak convolution (Sec. 1, "initial
+                         convolution" of Sec. 3)
+  fdk / fdk_slices       FDK backprojection, a weighted sum of P samples per
+                         voxel (Sec. 2.1)
+  bounds                 Eq. 1 at the four vertices of each square (Sec. 2.1)
+                         for the 4^s squares of Sec. 2.2
+  shift_decimate         shift + angular low-pass + downsample (Sec. 2.1)
+  fdkod / fdkod_slices   FDK-OD (Sec. 2.2)
+
+Every function here has at least one pin in tests/test_oracle_*.py that does
+not go through the oracle itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "crop window violated"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc, FP64, no FP contraction, OpenMP)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_c_int, _c_long, _c_double, _vp = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_void_p
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            sig = {
+                "oracle_set_threads": (None, [_c_int]),
+                "oracle_max_threads": (_c_int, []),
+                "oracle_filter_rows": (_c_int, [_c_double, _c_int, _c_int, _c_int, _vp, _c_long, _vp, _vp]),
+                "oracle_filter": (_c_int, [_c_double, _c_int, _c_int, _c_int, _vp, _vp]),
+                "oracle_fdk_slices": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _c_int,
+                                               _vp, _vp]),
+                "oracle_fdk": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
+                "oracle_bounds": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp,
+                                           _vp]),
+                "oracle_shift_decimate": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp,
+                                                   _c_int, _c_int, _vp]),
+                "oracle_fdkod_slices": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp,
+                                                 _c_int, _c_int, _vp, _vp]),
+                "oracle_fdkod": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int,
+                                          _vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what}: {ERRORS.get(rc, rc)}")
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _qarg(Q: np.ndarray):
+    if Q.dtype == np.float64:
+        return np.ascontiguousarray(Q), 1
+    return np.ascontiguousarray(Q, dtype=np.float32), 0
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def filter_rows(proj: np.ndarray, R: float, rows) -> np.ndarray:
+    """Filtered rows (flat index k*Nv + v) of proj[P][Nv][Nu] (float32)."""
+    proj = np.ascontiguousarray(proj, dtype=np.float32)
+    P, Nv, Nu = proj.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64).reshape(-1)
+    out = np.empty((rows.size, Nu), dtype=np.float64)
+    _check(_load().oracle_filter_rows(R, Nu, Nv, P, _ptr(proj), rows.size, _ptr(rows), _ptr(out)), "filter_rows")
+    return out
+
+
+def filter(proj: np.ndarray, R: float) -> np.ndarray:
+    proj = np.ascontiguousarray(proj, dtype=np.float32)
+    P, Nv, Nu = proj.shape
+    out = np.empty((P, Nv, Nu), dtype=np.float64)
+    _check(_load().oracle_filter(R, Nu, Nv, P, _ptr(proj), _ptr(out)), "filter")
+    return out
+
+
+def fdk_slices(Q: np.ndarray, R: float, N: int, zs) -> np.ndarray:
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    zs = np.ascontiguousarray(zs, dtype=np.int32).reshape(-1)
+    out = np.empty((zs.size, N, N), dtype=np.float64)
+    _check(_load().oracle_fdk_slices(R, N, Nu, Nv, P, _ptr(Q), f64, zs.size, _ptr(zs), _ptr(out)), "fdk_slices")
+    return out
+
+
+def fdk(Q: np.ndarray, R: float, N: int) -> np.ndarray:
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    out = np.empty((N, N, N), dtype=np.float64)
+    _check(_load().oracle_fdk(R, N, Nu, Nv, P, _ptr(Q), f64, _ptr(out)), "fdk")
+    return out
+
+
+def bounds(R: float, N: int, Nu: int, P: int, s: int) -> dict:
+    """Crop bounds per (square, angle): lo, hi, crop, phi [4^s][P]; w0, T [4^s]."""
+    nsq = 4 ** s
+    lo = np.empty((nsq, P), np.int32)
+    hi = np.empty((nsq, P), np.int32)
+    crop = np.empty((nsq, P), np.int32)
+    phi = np.empty((nsq, P), np.float64)
+    w0 = np.empty(nsq, np.int32)
+    T = np.empty(nsq, np.int32)
+    _check(_load().oracle_bounds(R, N, Nu, P, s, _ptr(lo), _ptr(hi), _ptr(crop), _ptr(phi), _ptr(w0), _ptr(T)),
+           "bounds")
+    return {"lo": lo, "hi": hi, "crop": crop, "phi": phi, "w0": w0, "T": T}
+
+
+def shift_decimate(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int) -> np.ndarray:
+    """Decomposed data S'_q[j][v][t] of square q (D > 1)."""
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    T = int(bounds(R, N, Nu, P, s)["T"][q])
+    out = np.empty((P // D, Nv, T), dtype=np.float64)
+    _check(_load().oracle_shift_decimate(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, q, _ptr(out)), "shift_decimate")
+    return out
+
+
+def fdkod_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, zs) -> np.ndarray:
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    zs = np.ascontiguousarray(zs, dtype=np.int32).reshape(-1)
+    out = np.empty((zs.size, N, N), dtype=np.float64)
+    _check(_load().oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, zs.size, _ptr(zs), _ptr(out)),
+           "fdkod_slices")
+    return out
+
+
+def fdkod(Q: np.ndarray, R: float, N: int, s: int, D: int) -> np.ndarray:
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    out = np.empty((N, N, N), dtype=np.float64)
+    _check(_load().oracle_fdkod(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, _ptr(out)), "fdkod")
+    return out
