@@ -1,0 +1,175 @@
+/*
+ * fdkod.h -- C ABI of the GB300 (sm_103a) FDK-OD cone-beam backprojection
+ * library, libfdkod.so.
+ *
+ * Method: Andriiashen & Kozhevnikov, "Fast optimal decomposed modification
+ * of FDK with potential decreasing of memory consuming" (2017).  FDK
+ * filters each detector row and backprojects every voxel as a weighted sum
+ * of P samples (Sec. 1, Sec. 2.1).  FDK-OD splits every slice into 4^s
+ * squares of side N/2^s (Sec. 2.2), bounds the detector columns each square
+ * needs per view with Eq. 1 at the square's vertices (Sec. 2.1), shifts the
+ * cropped rows so the square centre sits on one column, low-pass filters
+ * and downsamples them along the view axis by D (angular decimation,
+ * Sec. 2.1), and backprojects each square from the P/D remaining views.
+ *
+ * Conventions (shared by every entry point):
+ *  - lengths in voxels; voxel centres x_i = i - (N-1)/2 (same for y, z);
+ *  - views beta_k = 2 pi k / P, k = 0..P-1, over a full orbit; source at
+ *    -R (cos beta, sin beta, 0); R is the source-to-isocentre distance
+ *    that appears in Eq. 1;
+ *  - virtual flat detector through the isocentre with unit pitch, columns
+ *    u = 0..Nu-1, rows v = 0..Nv-1, a = u - (Nu-1)/2, b = v - (Nv-1)/2;
+ *  - projections proj[P][Nv][Nu] float32 (u fastest), filtered projections
+ *    Q[P][Nv][Nu] in the plan's storage type, volume vol[N][N][N] float32
+ *    indexed [z][y][x] (x fastest);
+ *  - every device pointer is a CUDA device address owned by the caller;
+ *    the library never frees or retains it after the call returns;
+ *  - `stream` is a cudaStream_t passed as an integer (0 = legacy default
+ *    stream); all device work of a call is enqueued on it and the call
+ *    returns without waiting, except where a function says it synchronises;
+ *  - there is no CPU fallback: every compute step runs in CUDA kernels.
+ *
+ * Errors: every int-returning function returns FDKOD_OK (0) or a negative
+ * fdkod_status; no function throws or aborts.  Asynchronous kernel faults
+ * surface as FDKOD_ERR_CUDA on a later call.  Kernels that detect an
+ * out-of-window access record it in a per-plan device status word instead
+ * of trapping; fdkod_last_device_status() reads and clears it.
+ */
+#ifndef FDKOD_H
+#define FDKOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDKOD_OK = 0,
+    FDKOD_ERR_INVALID_ARG = -1, /* null pointer, non-positive size, bad enum */
+    FDKOD_ERR_UNSUPPORTED = -2, /* D does not divide P, 2^s > N, source inside the volume, sizes over limits */
+    FDKOD_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    FDKOD_ERR_OOM = -4,         /* device or host allocation failed */
+    FDKOD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    FDKOD_ERR_BOUNDS = -6       /* a kernel's staging window was too small (result invalid) */
+} fdkod_status;
+
+/* Storage type of the filtered projections Q. */
+typedef enum { FDKOD_F32 = 0, FDKOD_BF16 = 1, FDKOD_F16 = 2 } fdkod_dtype;
+
+/* Circular-orbit cone-beam geometry (Sec. 2.1; R as in Eq. 1). */
+typedef struct {
+    double R;   /* source-to-isocentre distance, voxels; must exceed the volume's half-diagonal + 1 */
+    int32_t N;  /* volume is N x N x N voxels */
+    int32_t Nu; /* detector columns */
+    int32_t Nv; /* detector rows */
+    int32_t P;  /* views over 360 degrees */
+} fdkod_geometry;
+
+typedef struct fdkod_plan fdkod_plan_t;
+
+/* Read-only facts about a plan (sizes of its internal buffers). */
+typedef struct {
+    int32_t s, D, Pd;        /* decomposition level, decimation factor, P/D */
+    int32_t n_squares;       /* 4^s */
+    int32_t T_stride;        /* row stride (elements) of the decomposed data */
+    int32_t fft_length;      /* FFT length of the filter stage */
+    int64_t decomposed_elems;/* n_squares * Pd * Nv * T_stride (0 when D == 1) */
+    int64_t device_bytes;    /* device memory the plan holds */
+} fdkod_plan_info;
+
+/*
+ * Build a plan for geometry *g, decomposition level s (4^s squares of side
+ * N/2^s, Sec. 2.2) and decimation factor D (P/D views per square after the
+ * angular decimation of Sec. 2.1; D = 1 means crop only, which equals plain
+ * FDK).  qtype is the storage type fdkod_filter writes and the
+ * backprojections read.
+ *
+ * Computes, on the device in FP64, the per-(square, view) crop bounds of
+ * Eq. 1 at the square vertices, the shift centres and the shifted-row
+ * windows, and allocates the decomposed-data workspace.  Synchronises the
+ * device before returning.  On success *out owns all plan memory; release
+ * it with fdkod_destroy.  Errors: INVALID_ARG (null g/out, non-positive
+ * sizes, R <= 0, unknown qtype), UNSUPPORTED (P % D != 0, s < 0,
+ * s > 7, 2^s > N, R not beyond the volume, sizes above 2^15, Nu above
+ * 8192), OOM, CUDA.
+ */
+int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out);
+
+/* Release a plan (NULL is ignored).  Waits for the device to finish. */
+void fdkod_destroy(fdkod_plan_t *plan);
+
+/* Fill *info.  Errors: INVALID_ARG. */
+int fdkod_get_info(const fdkod_plan_t *plan, fdkod_plan_info *info);
+
+/*
+ * FDK filter stage (Sec. 1; the "initial convolution" of Sec. 3): for every
+ * detector row, q = proj * R / sqrt(R^2 + a^2 + b^2), then linear
+ * convolution along u with the discrete Ram-Lak kernel (h(0) = 1/4,
+ * h(n odd) = -1/(pi^2 n^2), h(n even) = 0), zero outside the detector.
+ * proj: device [P][Nv][Nu] float32.  Q: device [P][Nv][Nu] of the plan's
+ * qtype.  proj and Q must not overlap.  Errors: INVALID_ARG, CUDA.
+ */
+int fdkod_filter(fdkod_plan_t *plan, const float *proj, void *Q, uintptr_t stream);
+
+/*
+ * FDK-OD backprojection (Sec. 2.2): vol = for every square, the sum over
+ * the P/D decimated views beta_{jD} of U^-2 times the bilinear sample of
+ * the decomposed data at column t = u - phi - w0 and row z/U + (Nv-1)/2,
+ * scaled by pi / (P/D).  For D > 1 the decomposed data is first built in
+ * the plan's workspace (shift by linear interpolation, triangle low-pass
+ * (D-|i|)/D^2 circular over views, downsample by D; Sec. 2.1).  D = 1
+ * reads each square's crop of Q directly.  Q: device [P][Nv][Nu] qtype;
+ * vol: device [N][N][N] float32, fully overwritten.  Concurrent calls with
+ * the same plan race on its workspace.  Errors: INVALID_ARG, CUDA.
+ */
+int fdkod_backproject(fdkod_plan_t *plan, const void *Q, float *vol, uintptr_t stream);
+
+/*
+ * Plain FDK backprojection (Sec. 2.1, the baseline of the speedup):
+ * vol = (pi/P) sum_k U_k^-2 Q_k(u, v) over all P views with bilinear
+ * interpolation, u from Eq. 1 and v = z/U + (Nv-1)/2.  Same arguments,
+ * layouts and errors as fdkod_backproject.
+ */
+int fdk_backproject_plain(fdkod_plan_t *plan, const void *Q, float *vol, uintptr_t stream);
+
+/*
+ * The decomposition stage on its own (Sec. 2.1 shift + angular
+ * decimation): writes S'[q][j][v][t] (float32, t < T_stride, zero for
+ * t >= T[q]) for all squares q, decimated views j < P/D and rows v to the
+ * device buffer out of info.decomposed_elems floats.  For inspection and
+ * tests; fdkod_backproject uses the plan's own workspace.  Errors:
+ * INVALID_ARG (also when D == 1), CUDA.
+ */
+int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t stream);
+
+/*
+ * Copy the plan's crop bounds to host arrays (each may be NULL):
+ * lo, hi, crop [4^s][P] int32 (lo = floor(min u) and hi = floor(max u) + 1
+ * over the square's four vertex voxel centres, so linear interpolation at
+ * any voxel of the square reads columns lo..hi; crop = floor(phi + w0),
+ * the first column the shifted row reads); phi [4^s][P] float64, the column of
+ * the square centre's projection; w0, T [4^s] int32, the offset and width
+ * of the shifted rows (sample t sits at column phi + w0 + t).  Synchronises
+ * the device.  Errors: INVALID_ARG, CUDA.
+ */
+int fdkod_get_bounds(const fdkod_plan_t *plan, int32_t *lo, int32_t *hi, int32_t *crop,
+                     double *phi, int32_t *w0, int32_t *T);
+
+/*
+ * Read and clear the plan's device status word after the work queued on
+ * `stream` (synchronises the stream).  Returns FDKOD_OK, FDKOD_ERR_BOUNDS
+ * (a staging window overflowed; the affected output is invalid),
+ * FDKOD_ERR_TIMEOUT, or FDKOD_ERR_CUDA.
+ */
+int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
+
+/* Static message for a status code. */
+const char *fdkod_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDKOD_H */

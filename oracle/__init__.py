@@ -7,7 +7,8 @@ with -ffp-contract=off), and this module only marshals numpy arrays.
 
 Functions and the passages they follow:
   filter / filter_rows   cosine weight + Ram-Lak convolution (Sec. 1, "initial
-                         convolution" of Sec. 3)
+                         convolution" of Sec. 3), direct sums in C
+  filter_fft             the same convolution through numpy's FP64 FFT
   fdk / fdk_slices       FDK backprojection, a weighted sum of P samples per
                          voxel (Sec. 2.1)
   bounds                 Eq. 1 at the four vertices of each square (Sec. 2.1)
@@ -117,6 +118,32 @@ def filter(proj: np.ndarray, R: float) -> np.ndarray:
     P, Nv, Nu = proj.shape
     out = np.empty((P, Nv, Nu), dtype=np.float64)
     _check(_load().oracle_filter(R, Nu, Nv, P, _ptr(proj), _ptr(out)), "filter")
+    return out
+
+
+def filter_fft(proj: np.ndarray, R: float) -> np.ndarray:
+    """The same filter as ``filter`` (cosine weight + linear Ram-Lak
+    convolution, zero padding), computed with numpy's FP64 FFT: the kernel
+    is wrapped onto a circle of length L >= 2 Nu, where every lag of the
+    linear convolution keeps its own tap.  Fast enough for full-size views."""
+    proj = np.asarray(proj)
+    P, Nv, Nu = proj.shape
+    L = 1
+    while L < 2 * Nu:
+        L *= 2
+    lag = np.minimum(np.arange(L), L - np.arange(L))
+    h = np.zeros(L)
+    h[lag == 0] = 0.25
+    odd = lag % 2 == 1
+    h[odd] = -1.0 / (np.pi ** 2 * lag[odd].astype(np.float64) ** 2)
+    H = np.fft.rfft(h).real
+    a = np.arange(Nu) - (Nu - 1) / 2
+    b = np.arange(Nv) - (Nv - 1) / 2
+    w = R / np.sqrt(R * R + a[None, :] ** 2 + b[:, None] ** 2)
+    out = np.empty((P, Nv, Nu), dtype=np.float64)
+    for k in range(P):
+        q = proj[k].astype(np.float64) * w
+        out[k] = np.fft.irfft(np.fft.rfft(q, n=L, axis=-1) * H, n=L, axis=-1)[:, :Nu]
     return out
 
 

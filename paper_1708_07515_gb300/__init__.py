@@ -1,0 +1,22 @@
+"""GB300 (sm_103a) FDK-OD cone-beam backprojection.
+
+A thin ctypes binding over libfdkod.so, whose C ABI is include/fdkod.h.
+Every compute step runs in the library's CUDA kernels; this package only
+marshals torch device tensors (pointers, sizes, the current CUDA stream).
+There is no CPU fallback: if the library is missing, every call raises.
+"""
+from .fdkod import (  # noqa: F401
+    FDKOD_BF16,
+    FDKOD_F16,
+    FDKOD_F32,
+    FdkodError,
+    Plan,
+    fdk_backproject_plain,
+    fdkod_backproject,
+    fdkod_decompose,
+    fdkod_filter,
+    fdkod_get_bounds,
+    fdkod_plan,
+    lib_path,
+    load,
+)

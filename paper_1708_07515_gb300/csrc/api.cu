@@ -1,0 +1,332 @@
+// C ABI of libfdkod: plan construction (host-side validation, trig tables,
+// FFT tables, workspace sizing) and the entry points of include/fdkod.h.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "fdkod_internal.cuh"
+
+using namespace fdkod;
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FDKOD_OK;
+    return e == cudaErrorMemoryAllocation ? FDKOD_ERR_OOM : FDKOD_ERR_CUDA;
+}
+
+#define FDKOD_TRY(expr)                           \
+    do {                                          \
+        int _rc = cuda_status(expr);              \
+        if (_rc != FDKOD_OK) return _rc;          \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(PlanImpl &p, T **ptr, size_t n) {
+    cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * std::max<size_t>(n, 1));
+    if (e == cudaSuccess) p.device_bytes += (int64_t)(sizeof(T) * std::max<size_t>(n, 1));
+    return e;
+}
+
+void free_set(SquareSet &ss) {
+    cudaFree(ss.lo);
+    cudaFree(ss.hi);
+    cudaFree(ss.crop);
+    cudaFree(ss.w0);
+    cudaFree(ss.T);
+    cudaFree(ss.phi);
+    cudaFree(ss.geo);
+    ss = SquareSet{};
+}
+
+void free_plan(PlanImpl &p) {
+    free_set(p.od);
+    free_set(p.pl);
+    cudaFree(p.cs);
+    cudaFree(p.H);
+    cudaFree(p.tw);
+    cudaFree(p.Sp);
+    cudaFree(p.status);
+}
+
+double centre(int i, int n) { return (double)i - 0.5 * (double)(n - 1); }
+
+void square_range(int q, int m, int N, int &i0, int &i1) {
+    i0 = (int)(((long long)q * N + m - 1) / m);
+    i1 = (int)((((long long)q + 1) * N + m - 1) / m) - 1;
+}
+
+// Staging window of the backprojection kernel: the largest column and row
+// extent any 16 x 16 x kZT voxel tile of this square set can touch in one
+// view, from an FP64 sweep over all tiles and views (column coordinate
+// relative to the square centre; row extent bounded over all slabs).
+void size_windows(const PlanImpl &p, SquareSet &ss, const std::vector<double2> &cs) {
+    const double R = p.g.R;
+    const int N = p.g.N, P = p.g.P;
+    const int mside = (N + ss.m - 1) / ss.m;
+    ss.tiles_per_side = (mside + kTile - 1) / kTile;
+    double ext_t = 0.0, ext_v = 0.0;
+    const double zabs = 0.5 * (double)(N - 1);
+    for (int q = 0; q < ss.nsq; ++q) {
+        int ix0, ix1, iy0, iy1;
+        square_range(q % ss.m, ss.m, N, ix0, ix1);
+        square_range(q / ss.m, ss.m, N, iy0, iy1);
+        const double xc = 0.5 * (centre(ix0, N) + centre(ix1, N));
+        const double yc = 0.5 * (centre(iy0, N) + centre(iy1, N));
+        for (int ty = iy0; ty <= iy1; ty += kTile)
+            for (int tx = ix0; tx <= ix1; tx += kTile) {
+                const double xs[2] = {centre(tx, N), centre(std::min(tx + kTile - 1, ix1), N)};
+                const double ys[2] = {centre(ty, N), centre(std::min(ty + kTile - 1, iy1), N)};
+                for (int k = 0; k < P; ++k) {
+                    const double cb = cs[k].x, sb = cs[k].y;
+                    const double ac = R * (yc * cb - xc * sb) / (R + xc * cb + yc * sb);
+                    double tmin = 1e300, tmax = -1e300, umin = 1e300, umax = -1e300;
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b) {
+                            const double den = R + xs[a] * cb + ys[b] * sb;
+                            const double t = R * (ys[b] * cb - xs[a] * sb) / den - ac;
+                            const double iu = R / den;
+                            tmin = std::min(tmin, t);
+                            tmax = std::max(tmax, t);
+                            umin = std::min(umin, iu);
+                            umax = std::max(umax, iu);
+                        }
+                    ext_t = std::max(ext_t, tmax - tmin);
+                    ext_v = std::max(ext_v, (double)(kZT - 1) * umax + zabs * (umax - umin));
+                }
+            }
+    }
+    // floor(max) - floor(min) <= ceil(extent); +2 for the interpolation
+    // neighbour and the one-sample margin below; +2 for FP32 rounding slack
+    ss.Wd = (int)ceil(ext_t) + 5;
+    ss.Wd += ss.Wd & 1;  // even width: odd shared-memory row stride
+    ss.Rw = (int)ceil(ext_v) + 5;
+}
+
+int make_set(PlanImpl &p, SquareSet &ss, int s, cudaStream_t st, const std::vector<double2> &cs) {
+    ss.s = s;
+    ss.m = 1 << s;
+    ss.nsq = ss.m * ss.m;
+    const size_t n = (size_t)ss.nsq * p.g.P;
+    FDKOD_TRY(dalloc(p, &ss.lo, n));
+    FDKOD_TRY(dalloc(p, &ss.hi, n));
+    FDKOD_TRY(dalloc(p, &ss.crop, n));
+    FDKOD_TRY(dalloc(p, &ss.phi, n));
+    FDKOD_TRY(dalloc(p, &ss.geo, n));
+    FDKOD_TRY(dalloc(p, &ss.w0, (size_t)ss.nsq));
+    FDKOD_TRY(dalloc(p, &ss.T, (size_t)ss.nsq));
+    FDKOD_TRY(launch_bounds(p, ss, st));
+    std::vector<int32_t> T(ss.nsq);
+    FDKOD_TRY(cudaMemcpyAsync(T.data(), ss.T, sizeof(int32_t) * ss.nsq, cudaMemcpyDeviceToHost, st));
+    FDKOD_TRY(cudaStreamSynchronize(st));
+    ss.Tmax = *std::max_element(T.begin(), T.end());
+    size_windows(p, ss, cs);
+    return FDKOD_OK;
+}
+
+// Discrete Ram-Lak kernel, unit sample spacing.
+double ramlak(long n) {
+    if (n == 0) return 0.25;
+    if (n % 2 == 0) return 0.0;
+    return -1.0 / (M_PI * M_PI * (double)n * (double)n);
+}
+
+int make_fft_tables(PlanImpl &p, cudaStream_t st) {
+    int L = 1, lg = 0;
+    while (L < 2 * p.g.Nu) {
+        L <<= 1;
+        ++lg;
+    }
+    if (L < 4) {
+        L = 4;
+        lg = 2;
+    }
+    p.L = L;
+    p.log2L = lg;
+    // kernel wrapped onto the circle of length L (taps |n| <= L/2); as
+    // L >= 2 Nu every product of the linear convolution sits at its own lag
+    std::vector<double> ctab(L);
+    for (int i = 0; i < L; ++i) ctab[i] = cos(2.0 * M_PI * (double)i / (double)L);
+    std::vector<float> H(L);
+    for (int k = 0; k < L; ++k) {
+        double acc = ramlak(0);
+        for (int n = 1; n < L / 2; n += 2) acc += 2.0 * ramlak(n) * ctab[(size_t)((long long)k * n % L)];
+        acc += ramlak(L / 2) * ctab[(size_t)((long long)k * (L / 2) % L)];
+        H[k] = (float)(acc / (double)L);
+    }
+    std::vector<float2> tw(L / 2);
+    for (int i = 0; i < L / 2; ++i) {
+        const double a = 2.0 * M_PI * (double)i / (double)L;
+        tw[i] = make_float2((float)cos(a), (float)(-sin(a)));
+    }
+    FDKOD_TRY(dalloc(p, &p.H, (size_t)L));
+    FDKOD_TRY(dalloc(p, &p.tw, (size_t)L / 2));
+    FDKOD_TRY(cudaMemcpyAsync(p.H, H.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
+    FDKOD_TRY(cudaMemcpyAsync(p.tw, tw.data(), sizeof(float2) * (L / 2), cudaMemcpyHostToDevice, st));
+    FDKOD_TRY(cudaStreamSynchronize(st));
+    return FDKOD_OK;
+}
+
+int build_plan(PlanImpl &p, cudaStream_t st) {
+    const int P = p.g.P;
+    std::vector<double2> cs(P);
+    for (int k = 0; k < P; ++k) {
+        const double beta = 2.0 * M_PI * (double)k / (double)P;
+        cs[k] = make_double2(cos(beta), sin(beta));
+    }
+    FDKOD_TRY(dalloc(p, &p.cs, (size_t)P));
+    FDKOD_TRY(cudaMemcpyAsync(p.cs, cs.data(), sizeof(double2) * P, cudaMemcpyHostToDevice, st));
+    FDKOD_TRY(dalloc(p, &p.status, 1));
+    FDKOD_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), st));
+    int rc = make_set(p, p.od, p.s, st, cs);
+    if (rc) return rc;
+    // plain FDK tiling: squares of 64..127 voxels a side (whole slice when
+    // N < 128), cut into 16 x 16 tiles
+    int sp = 0;
+    while ((p.g.N >> (sp + 1)) >= 64 && sp < 7) ++sp;
+    rc = make_set(p, p.pl, sp, st, cs);
+    if (rc) return rc;
+    rc = make_fft_tables(p, st);
+    if (rc) return rc;
+    p.Tstride = (p.od.Tmax + 3) & ~3;
+    if (p.D > 1) {
+        p.sp_elems = (int64_t)p.od.nsq * p.Pd * p.g.Nv * p.Tstride;
+        FDKOD_TRY(dalloc(p, &p.Sp, (size_t)p.sp_elems));
+    }
+    FDKOD_TRY(cudaStreamSynchronize(st));
+    return FDKOD_OK;
+}
+
+bool valid_dtype(int t) { return t == FDKOD_F32 || t == FDKOD_BF16 || t == FDKOD_F16; }
+
+}  // namespace
+
+extern "C" {
+
+int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out) {
+    if (!g || !out) return FDKOD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!(g->R > 0.0) || g->N <= 0 || g->Nu <= 0 || g->Nv <= 0 || g->P <= 0 || D <= 0 || !valid_dtype(qtype))
+        return FDKOD_ERR_INVALID_ARG;
+    const int lim = 1 << 15;
+    if (g->N > lim || g->Nu > lim || g->Nv > lim || g->P > lim) return FDKOD_ERR_UNSUPPORTED;
+    // the filter's shared-memory FFT holds 2^ceil(log2(2 Nu)) complex floats
+    if (g->Nu > 8192) return FDKOD_ERR_UNSUPPORTED;
+    if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0) return FDKOD_ERR_UNSUPPORTED;
+    // the source must lie outside the volume's circumscribed cylinder
+    if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;
+    fdkod_plan_t *pl = new (std::nothrow) fdkod_plan_t;
+    if (!pl) return FDKOD_ERR_OOM;
+    PlanImpl &p = pl->impl;
+    p.g = *g;
+    p.s = s;
+    p.D = D;
+    p.Pd = g->P / D;
+    p.qtype = qtype;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete pl;
+        return FDKOD_ERR_CUDA;
+    }
+    int rc = build_plan(p, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc != FDKOD_OK) {
+        free_plan(p);
+        delete pl;
+        return rc;
+    }
+    *out = pl;
+    return FDKOD_OK;
+}
+
+void fdkod_destroy(fdkod_plan_t *plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan(plan->impl);
+    delete plan;
+}
+
+int fdkod_get_info(const fdkod_plan_t *plan, fdkod_plan_info *info) {
+    if (!plan || !info) return FDKOD_ERR_INVALID_ARG;
+    const PlanImpl &p = plan->impl;
+    info->s = p.s;
+    info->D = p.D;
+    info->Pd = p.Pd;
+    info->n_squares = p.od.nsq;
+    info->T_stride = p.Tstride;
+    info->fft_length = p.L;
+    info->decomposed_elems = (int64_t)p.od.nsq * p.Pd * p.g.Nv * p.Tstride * (p.D > 1 ? 1 : 0);
+    info->device_bytes = p.device_bytes;
+    return FDKOD_OK;
+}
+
+int fdkod_filter(fdkod_plan_t *plan, const float *proj, void *Q, uintptr_t stream) {
+    if (!plan || !proj || !Q) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(launch_filter(plan->impl, proj, Q, (cudaStream_t)stream));
+}
+
+int fdkod_backproject(fdkod_plan_t *plan, const void *Q, float *vol, uintptr_t stream) {
+    if (!plan || !Q || !vol) return FDKOD_ERR_INVALID_ARG;
+    PlanImpl &p = plan->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p.D == 1) return cuda_status(launch_backproject(p, p.od, true, Q, vol, st));
+    FDKOD_TRY(launch_decompose(p, Q, p.Sp, st));
+    return cuda_status(launch_backproject(p, p.od, false, p.Sp, vol, st));
+}
+
+int fdk_backproject_plain(fdkod_plan_t *plan, const void *Q, float *vol, uintptr_t stream) {
+    if (!plan || !Q || !vol) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(launch_backproject(plan->impl, plan->impl.pl, true, Q, vol, (cudaStream_t)stream));
+}
+
+int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t stream) {
+    if (!plan || !Q || !out || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(launch_decompose(plan->impl, Q, out, (cudaStream_t)stream));
+}
+
+int fdkod_get_bounds(const fdkod_plan_t *plan, int32_t *lo, int32_t *hi, int32_t *crop, double *phi,
+                     int32_t *w0, int32_t *T) {
+    if (!plan) return FDKOD_ERR_INVALID_ARG;
+    const PlanImpl &p = plan->impl;
+    const size_t n = (size_t)p.od.nsq * p.g.P;
+    FDKOD_TRY(cudaDeviceSynchronize());
+    if (lo) FDKOD_TRY(cudaMemcpy(lo, p.od.lo, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (hi) FDKOD_TRY(cudaMemcpy(hi, p.od.hi, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (crop) FDKOD_TRY(cudaMemcpy(crop, p.od.crop, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (phi) FDKOD_TRY(cudaMemcpy(phi, p.od.phi, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (w0) FDKOD_TRY(cudaMemcpy(w0, p.od.w0, sizeof(int32_t) * p.od.nsq, cudaMemcpyDeviceToHost));
+    if (T) FDKOD_TRY(cudaMemcpy(T, p.od.T, sizeof(int32_t) * p.od.nsq, cudaMemcpyDeviceToHost));
+    return FDKOD_OK;
+}
+
+int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream) {
+    if (!plan) return FDKOD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    FDKOD_TRY(cudaMemcpyAsync(&h, plan->impl.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FDKOD_TRY(cudaMemsetAsync(plan->impl.status, 0, sizeof(int), st));
+    FDKOD_TRY(cudaStreamSynchronize(st));
+    if (h & 2) return FDKOD_ERR_TIMEOUT;
+    if (h & 1) return FDKOD_ERR_BOUNDS;
+    return FDKOD_OK;
+}
+
+const char *fdkod_strerror(int status) {
+    switch (status) {
+        case FDKOD_OK: return "ok";
+        case FDKOD_ERR_INVALID_ARG: return "invalid argument";
+        case FDKOD_ERR_UNSUPPORTED: return "unsupported configuration";
+        case FDKOD_ERR_CUDA: return "CUDA error";
+        case FDKOD_ERR_OOM: return "out of memory";
+        case FDKOD_ERR_TIMEOUT: return "device wait timed out";
+        case FDKOD_ERR_BOUNDS: return "staging window overflow";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

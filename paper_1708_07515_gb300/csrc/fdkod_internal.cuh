@@ -1,0 +1,74 @@
+// Internal declarations shared by the CUDA translation units of libfdkod.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdkod.h"
+
+namespace fdkod {
+
+// Per-(square, view) backprojection geometry, from FP64 values computed by
+// the bound kernel.  With (dx, dy) a voxel's offset from the square centre
+// (x_c, y_c) and d_c = R + x_c cos b + y_c sin b:
+//   g = R / d_c (1/U at the centre, kept in FP64 for the row origin),
+//   r = 1 / d_c,  e = a_c / R,  alpha = -sin b - e cos b,  gamma = cos b - e sin b,
+//   1/U = g / (1 + r (cb dx + sb dy)),
+//   a(x, y) - a(x_c, y_c) = (1/U) (alpha dx + gamma dy)      (Eq. 1 rearranged),
+// so the kernels work with small square-local numbers in FP32.
+// frac = (phi + w0) - floor(phi + w0), the sub-pixel part of the shift.
+struct GeomEntry {
+    double g;
+    float cb, sb, r, alpha, gamma, frac;
+};
+static_assert(sizeof(GeomEntry) == 32, "GeomEntry layout");
+
+// One decomposition of the slice into m x m squares (m = 2^s) with its
+// per-square, per-view tables on the device.
+struct SquareSet {
+    int s = 0, m = 1, nsq = 1;
+    int32_t *lo = nullptr, *hi = nullptr, *crop = nullptr, *w0 = nullptr, *T = nullptr;
+    double *phi = nullptr;
+    GeomEntry *geo = nullptr;
+    int32_t Tmax = 0;
+    // staging window of the backprojection kernel (elements), from a host
+    // FP64 sweep over every tile and view
+    int Wd = 0, Rw = 0;
+    int tiles_per_side = 1;  // 16-voxel tiles per square side
+};
+
+constexpr int kTile = 16;      // tile side in x and y (threads per CTA = 256)
+constexpr int kZT = 16;        // z voxels per thread
+constexpr int kViewsPerChunk = 8;
+
+struct PlanImpl {
+    fdkod_geometry g{};
+    int s = 0, D = 1, Pd = 1;
+    fdkod_dtype qtype = FDKOD_F32;
+    double2 *cs = nullptr;     // cos/sin of every view (host libm)
+    SquareSet od;              // FDK-OD squares (level s)
+    SquareSet pl;              // tiling used by the plain FDK baseline
+    // filter stage
+    int L = 0, log2L = 0;
+    float *H = nullptr;        // ramp spectrum / L, real and even
+    float2 *tw = nullptr;      // e^{-2 pi i m / L}, m < L/2
+    // decomposed data S'[q][j][v][t]
+    float *Sp = nullptr;
+    int Tstride = 0;
+    int64_t sp_elems = 0;
+    int *status = nullptr;     // device status word
+    int64_t device_bytes = 0;
+};
+
+// kernel launchers (return cudaError_t of the launch)
+cudaError_t launch_bounds(const PlanImpl &p, SquareSet &ss, cudaStream_t st);
+cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st);
+cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st);
+cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
+                               float *vol, cudaStream_t st);
+
+}  // namespace fdkod
+
+struct fdkod_plan {
+    fdkod::PlanImpl impl;
+};

@@ -1,0 +1,209 @@
+"""ctypes binding of libfdkod.so (include/fdkod.h), argument marshalling only.
+
+Functions carry the C names; ``Plan`` bundles them for a plan's lifetime.
+Tensors are torch CUDA tensors; the stream defaults to torch's current
+stream on the tensor's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libfdkod.so")
+_lock = threading.Lock()
+_lib = None
+
+FDKOD_F32, FDKOD_BF16, FDKOD_F16 = 0, 1, 2
+_DTYPES = {"f32": FDKOD_F32, "bf16": FDKOD_BF16, "f16": FDKOD_F16}
+
+
+class FdkodError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _load().fdkod_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("N", ctypes.c_int32), ("Nu", ctypes.c_int32), ("Nv", ctypes.c_int32),
+                ("P", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("D", ctypes.c_int32), ("Pd", ctypes.c_int32), ("n_squares", ctypes.c_int32),
+                ("T_stride", ctypes.c_int32), ("fft_length", ctypes.c_int32), ("decomposed_elems", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libfdkod.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"{_LIB_PATH} is not built; the CUDA library is required (no CPU fallback)")
+            lib = ctypes.CDLL(_LIB_PATH)
+            vp, i, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            sig = {
+                "fdkod_plan": (i, [ctypes.POINTER(Geometry), i, i, i, ctypes.POINTER(vp)]),
+                "fdkod_destroy": (None, [vp]),
+                "fdkod_get_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
+                "fdkod_filter": (i, [vp, vp, vp, u]),
+                "fdkod_backproject": (i, [vp, vp, vp, u]),
+                "fdk_backproject_plain": (i, [vp, vp, vp, u]),
+                "fdkod_decompose": (i, [vp, vp, vp, u]),
+                "fdkod_get_bounds": (i, [vp, vp, vp, vp, vp, vp, vp]),
+                "fdkod_last_device_status": (i, [vp, u]),
+                "fdkod_strerror": (ctypes.c_char_p, [i]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+_load = load
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise FdkodError(rc, what)
+
+
+def _stream(t, stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    return int(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _dev_ptr(t, what):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- C-named functions -------------------------------------------------------
+
+def fdkod_plan(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: int = FDKOD_F32) -> int:
+    g = Geometry(float(R), int(N), int(Nu), int(Nv), int(P))
+    out = ctypes.c_void_p()
+    _check(load().fdkod_plan(ctypes.byref(g), int(s), int(D), int(qtype), ctypes.byref(out)), "fdkod_plan")
+    return out.value
+
+
+def fdkod_filter(plan: int, proj, Q, stream=None) -> None:
+    _check(load().fdkod_filter(plan, _dev_ptr(proj, "proj"), _dev_ptr(Q, "Q"), _stream(proj, stream)),
+           "fdkod_filter")
+
+
+def fdkod_backproject(plan: int, Q, vol, stream=None) -> None:
+    _check(load().fdkod_backproject(plan, _dev_ptr(Q, "Q"), _dev_ptr(vol, "vol"), _stream(Q, stream)),
+           "fdkod_backproject")
+
+
+def fdk_backproject_plain(plan: int, Q, vol, stream=None) -> None:
+    _check(load().fdk_backproject_plain(plan, _dev_ptr(Q, "Q"), _dev_ptr(vol, "vol"), _stream(Q, stream)),
+           "fdk_backproject_plain")
+
+
+def fdkod_decompose(plan: int, Q, out, stream=None) -> None:
+    _check(load().fdkod_decompose(plan, _dev_ptr(Q, "Q"), _dev_ptr(out, "out"), _stream(Q, stream)),
+           "fdkod_decompose")
+
+
+def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
+    lo = np.empty((n_squares, P), np.int32)
+    hi = np.empty((n_squares, P), np.int32)
+    crop = np.empty((n_squares, P), np.int32)
+    phi = np.empty((n_squares, P), np.float64)
+    w0 = np.empty(n_squares, np.int32)
+    T = np.empty(n_squares, np.int32)
+    p = [ctypes.c_void_p(a.ctypes.data) for a in (lo, hi, crop, phi, w0, T)]
+    _check(load().fdkod_get_bounds(plan, *p), "fdkod_get_bounds")
+    return {"lo": lo, "hi": hi, "crop": crop, "phi": phi, "w0": w0, "T": T}
+
+
+# ---- convenience wrapper --------------------------------------------------
+
+class Plan:
+    """A plan for one geometry, decomposition level s and decimation D."""
+
+    def __init__(self, R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: str = "f32"):
+        self.R, self.N, self.Nu, self.Nv, self.P, self.s, self.D = float(R), N, Nu, Nv, P, s, D
+        self.qtype = qtype
+        self.handle = fdkod_plan(R, N, Nu, Nv, P, s, D, _DTYPES[qtype])
+        info = PlanInfo()
+        _check(load().fdkod_get_info(self.handle, ctypes.byref(info)), "fdkod_get_info")
+        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().fdkod_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def q_torch_dtype(self):
+        import torch
+        return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[self.qtype]
+
+    def filter(self, proj, Q=None, stream=None):
+        import torch
+        if Q is None:
+            Q = torch.empty((self.P, self.Nv, self.Nu), dtype=self.q_torch_dtype, device=proj.device)
+        fdkod_filter(self.handle, proj, Q, stream)
+        return Q
+
+    def _vol(self, Q, vol):
+        import torch
+        if vol is None:
+            vol = torch.empty((self.N, self.N, self.N), dtype=torch.float32, device=Q.device)
+        return vol
+
+    def backproject(self, Q, vol=None, stream=None):
+        vol = self._vol(Q, vol)
+        fdkod_backproject(self.handle, Q, vol, stream)
+        return vol
+
+    def backproject_plain(self, Q, vol=None, stream=None):
+        vol = self._vol(Q, vol)
+        fdk_backproject_plain(self.handle, Q, vol, stream)
+        return vol
+
+    def decompose(self, Q, out=None, stream=None):
+        import torch
+        shape = (self.info["n_squares"], self.info["Pd"], self.Nv, self.info["T_stride"])
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=Q.device)
+        fdkod_decompose(self.handle, Q, out, stream)
+        return out
+
+    def bounds(self) -> dict:
+        return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)
+
+    def device_status(self, stream=None) -> int:
+        import torch
+        st = int(torch.cuda.current_stream().cuda_stream) if stream is None else int(stream)
+        return int(load().fdkod_last_device_status(self.handle, st))

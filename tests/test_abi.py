@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads and exports every entry point
+include/fdkod.h declares; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1708_07515_gb300 import build, fdkod
+    build.build()
+    return fdkod.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fdkod.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:fdkod|fdk)_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert {"fdkod_plan", "fdkod_filter", "fdkod_backproject", "fdk_backproject_plain"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    from paper_1708_07515_gb300 import fdkod as F
+    out = ctypes.c_void_p()
+    assert lib.fdkod_plan(None, 1, 1, 0, ctypes.byref(out)) == -1
+    bad = [
+        (F.Geometry(64.0, 0, 16, 16, 8), 1, 1, 0, -1),     # N = 0 (empty volume)
+        (F.Geometry(64.0, 16, 16, 16, 0), 1, 1, 0, -1),    # no views
+        (F.Geometry(-1.0, 16, 16, 16, 8), 1, 1, 0, -1),    # R <= 0
+        (F.Geometry(64.0, 16, 16, 16, 8), 1, 1, 7, -1),    # unknown storage type
+        (F.Geometry(64.0, 16, 16, 16, 8), 1, 3, 0, -2),    # D does not divide P
+        (F.Geometry(64.0, 16, 16, 16, 8), 5, 1, 0, -2),    # 2^s > N
+        (F.Geometry(10.0, 16, 16, 16, 8), 1, 1, 0, -2),    # source inside the volume
+        (F.Geometry(64.0, 16, 16, 16, 8), -1, 1, 0, -2),   # negative s
+    ]
+    for g, s, D, qt, want in bad:
+        assert lib.fdkod_plan(ctypes.byref(g), s, D, qt, ctypes.byref(out)) == want, (g.N, s, D, qt)
+        assert out.value is None
+    for rc in (0, -1, -2, -3, -4, -5, -6, 99):
+        assert lib.fdkod_strerror(rc)
+    assert lib.fdkod_filter(None, None, None, 0) == -1
+    assert lib.fdkod_backproject(None, None, None, 0) == -1
+    assert lib.fdk_backproject_plain(None, None, None, 0) == -1
+    assert lib.fdkod_get_info(None, None) == -1
+    lib.fdkod_destroy(None)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    from paper_1708_07515_gb300 import fdkod as F
+    monkeypatch.setattr(F, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(F, "_lib", None)
+    with pytest.raises(RuntimeError):
+        F.load()

@@ -76,3 +76,13 @@ def test_matches_fft_convolution_with_ramp_spectrum(oracle_mod):
     X = np.fft.fft(q, n=L, axis=-1)
     y = np.real(np.fft.ifft(X * H, axis=-1))[..., :Nu]
     assert np.abs(Q - y).max() < 1e-8
+
+
+@pytest.mark.parametrize("Nu,Nv", [(17, 5), (64, 3), (100, 7)])
+def test_fft_form_equals_direct_convolution(oracle_mod, Nu, Nv):
+    rng = np.random.default_rng(Nu)
+    proj = (10 * rng.random((3, Nv, Nu))).astype(np.float32)
+    R = 3.0 * Nu
+    a = oracle_mod.filter(proj, R)
+    b = oracle_mod.filter_fft(proj, R)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-12 * np.abs(proj).max())
