@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the FDK-OD hot path on GB300.
+
+One step = one pass of the whole path over one synthetic scan: the FP64
+bound kernel (Eq. 1 at square vertices), the FFT ramp filter, the
+decomposition (shift + angular decimation) and the per-square
+backprojection.  Workload: 512^3 volume from 720 views of a 512^2 detector,
+s = 3, D = 4, 40 seeded random ellipsoids + 1 % Gaussian noise (synthetic
+stand-in for the paper's phantom and scanner data).
+
+Metric: effective voxel-updates/s = N^3 P / t_step (the plain-FDK-equivalent
+work; FDK-OD performs N^3 P / D updates).  The plain FDK baseline runs the
+same filter plus the plain backprojection on the same GPU.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank reconstructs its own independent scan (weak
+scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDK-OD voxel-updates/s vs plain FDK on one GB300 at fixed RMSE vs FP64 oracle"
+UNIT = "voxel-updates/s"
+WORKLOAD_KEY = "fdkod_512"
+# FP32 operations per voxel update of the backprojection's inner loop:
+# row coordinate (FMA, 2), fraction (1), three lerps (sub + FMA, 3 each),
+# weighted accumulate (FMA, 2)
+FLOP_PER_UPDATE = 14
+# on-chip bytes per update: the four float32 samples of the bilinear gather
+SMEM_BYTES_PER_UPDATE = 16
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD_KEY)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def rows_for_slices(N, Nv, R, zs):
+    """Detector rows the given slices can touch (b formula of Sec. 2.2 with
+    U in [1 - r/R, 1 + r/R])."""
+    rmax = math.sqrt(2.0) * 0.5 * (N - 1)
+    vc = 0.5 * (Nv - 1)
+    need = set()
+    for zi in zs:
+        z = zi - 0.5 * (N - 1)
+        va, vb = z / (1 - rmax / R) + vc, z / (1 + rmax / R) + vc
+        for r in range(int(math.floor(min(va, vb))) - 1, int(math.floor(max(va, vb))) + 3):
+            if 0 <= r < Nv:
+                need.add(r)
+    return sorted(need)
+
+
+def oracle_sample(w, proj, zs, oracle):
+    """The FP64 oracle on a bounded sample: filter the rows the slices need
+    (direct convolution), then FDK-OD on those slices.  Returns seconds."""
+    rows = rows_for_slices(w.N, w.Nv, w.R, zs)
+    flat = np.array([k * w.Nv + v for k in range(w.P) for v in rows], dtype=np.int64)
+    t0 = time.perf_counter()
+    Qr = oracle.filter_rows(proj, w.R, flat)
+    Q = np.zeros((w.P, w.Nv, w.Nu), dtype=np.float64)
+    Q.reshape(-1, w.Nu)[flat] = Qr
+    oracle.fdkod_slices(Q, w.R, w.N, w.s, w.D, zs)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The oracle as it stands, timed on the host cores: each step is a
+    bounded sample (one central slice) of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import phantom
+    oracle.build()
+    w = phantom.WORKLOADS[args.workload]
+    proj = phantom.make_projections(w)
+    cores = oracle.max_threads()
+    order = np.random.default_rng(w.seed).permutation(w.N)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_sample(w, proj, [int(order[i % w.N])], oracle)
+        if i >= args.warmup:
+            times.append(t)
+    per_step = sum(times) / len(times)
+    value = w.N * w.N * w.P / per_step
+    sample = (f"one seeded slice of {w.name} per step: FP64 direct-convolution filter of the rows it needs + "
+              "FP64 FDK-OD of the slice")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "P": w.P, "s": w.s, "D": w.D},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1708_07515_gb300 as fd
+    import phantom
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = phantom.WORKLOADS[args.workload]
+    # each rank reconstructs its own scan (independent problems, weak scaling)
+    ell = phantom.make_phantom(w.seed + rank, w.N, w.n_ell)
+    proj = phantom.project(ell, w.R, w.Nu, w.Nv, w.P)
+    if w.noise:
+        phantom.add_noise(proj, w.noise, w.seed + rank)
+
+    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D)
+    info = plan.info
+    stream = torch.cuda.current_stream()
+    proj_d = torch.from_numpy(proj).cuda()
+    Q = torch.empty((w.P, w.Nv, w.Nu), dtype=torch.float32, device="cuda")
+    S = torch.empty((info["n_squares"], info["Pd"], w.Nv, info["T_stride"]), dtype=torch.float32, device="cuda")
+    vol = torch.empty((w.N, w.N, w.N), dtype=torch.float32, device="cuda")
+    upd_eff = float(w.N) ** 3 * w.P
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        plan.compute_bounds()
+        if ev is not None:
+            ev[1].record(stream)
+        plan.filter(proj_d, Q)
+        if ev is not None:
+            ev[2].record(stream)
+        plan.decompose(Q, S)
+        if ev is not None:
+            ev[3].record(stream)
+        plan.backproject_decomposed(S, vol)
+        if ev is not None:
+            ev[4].record(stream)
+
+    launches_per_step = 4
+    # --- device-resident timed region
+    for _ in range(args.warmup):
+        step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms_local = t0.elapsed_time(t1)
+    stages = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs)
+              for i, name in enumerate(["bounds", "filter", "decompose", "backproject"])}
+    assert plan.device_status() == 0, "staging window overflow"
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_total = max_over_ranks(ms_local)
+    ms_step = ms_total / args.steps
+    value = world * upd_eff / (ms_step * 1e-3)
+
+    # --- plain FDK on the same GPU and data (filter + plain backprojection)
+    def plain_step():
+        plan.filter(proj_d, Q)
+        plan.backproject_plain(Q, vol)
+
+    for _ in range(max(1, args.warmup)):
+        plain_step()
+    n_plain = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_plain):
+        plain_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = max_over_ranks(a.elapsed_time(b)) / n_plain
+
+    # --- end to end through the public API with host buffers
+    proj_h = torch.from_numpy(proj).pin_memory()
+    vol_h = torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        proj_d.copy_(proj_h, non_blocking=True)
+        plan.compute_bounds()
+        plan.filter(proj_d, Q)
+        plan.backproject(Q, vol)
+        vol_h.copy_(vol, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    n_e2e = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(a.elapsed_time(b)) / n_e2e
+
+    # --- accuracy at the measured configuration, against the FP64 oracle
+    extra = {}
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        vol_od = plan.backproject(Q).cpu().numpy()
+        zs = [w.N // 2 - 1, w.N // 2]
+        rows = rows_for_slices(w.N, w.Nv, w.R, zs)
+        flat = np.array([k * w.Nv + v for k in range(w.P) for v in rows], dtype=np.int64)
+        Qo = np.zeros((w.P, w.Nv, w.Nu))
+        Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
+        ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
+        ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs)
+        g = vol_od[zs].astype(np.float64)
+        extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(g - ref_od) / np.linalg.norm(ref_od))
+        extra["rel_rmse_vs_fp64_fdk_oracle"] = float(np.linalg.norm(g - ref_fdk) / np.linalg.norm(ref_fdk))
+        extra["accuracy_slices"] = zs
+        if not args.no_cpu_baseline:
+            # seeded slices, one at a time, until about 10 s of oracle work
+            order = np.random.default_rng(w.seed).permutation(w.N)
+            done, t = [], 0.0
+            while t < 10.0 and len(done) < min(64, w.N):
+                z = int(order[len(done)])
+                t += oracle_sample(w, proj, [z], oracle)
+                done.append(z)
+            cpu = {"value": len(done) * w.N * w.N * w.P / t, "unit": UNIT, "cores": oracle.max_threads(),
+                   "kind": "oracle",
+                   "sample": f"{len(done)} seeded slices of {w.name}, each: FP64 direct-convolution filter of "
+                             f"the rows it needs + FP64 FDK-OD of the slice ({t:.1f} s total)"}
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    bp_ms = stages["backproject"]
+    upd_bp = float(w.N) ** 3 * (w.P // w.D)
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tflops = GB300_SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    achieved_tflops = FLOP_PER_UPDATE * upd_bp / (bp_ms * 1e-3) / 1e12
+    smem_peak = GB300_SMS * SMEM_BYTES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9
+    smem_ach = SMEM_BYTES_PER_UPDATE * upd_bp / (bp_ms * 1e-3) / 1e9
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded random-ellipsoid phantom, exact cone-beam projections, 1% Gaussian noise",
+            "config": {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s,
+                       "D": w.D, "step": "bounds + filter + decompose + backproject",
+                       "l2": "inputs larger than L2 (projections 755 MB, decomposed data "
+                             f"{info['decomposed_elems'] * 4 / 1e9:.2f} GB)",
+                       "parallelism": f"{world} independent scans, one per GPU"},
+            "e2e": {"value": world * upd_eff / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": proj_h.numel() * 4, "d2h_bytes_per_step": vol_h.numel() * 4,
+                    "ms_per_step": ms_e2e},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "alu", "kernel": "bp_kernel (FDK-OD backprojection)",
+                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "peak_note": f"152 SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
+                         "per_launch_updates": upd_bp, "flop_per_update": FLOP_PER_UPDATE,
+                         "avg_launch_ms": bp_ms},
+            "roofline_smem": {"achieved": smem_ach, "peak": smem_peak, "unit": "GB/s", "frac": smem_ach / smem_peak,
+                              "bytes_per_update": SMEM_BYTES_PER_UPDATE},
+            "stages_ms": stages,
+            "plain_fdk": {"value": world * upd_eff / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                          "step": "filter + plain backprojection"},
+            "speedup_vs_plain_fdk": ms_plain / ms_step,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        out.update(extra)
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

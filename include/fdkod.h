@@ -145,6 +145,25 @@ int fdk_backproject_plain(fdkod_plan_t *plan, const void *Q, float *vol, uintptr
 int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t stream);
 
 /*
+ * Backprojection stage of FDK-OD on its own: the same sum as
+ * fdkod_backproject for D > 1, reading decomposed data S (device, the
+ * layout fdkod_decompose writes) instead of the plan's workspace.  With
+ * fdkod_decompose it splits fdkod_backproject into its two kernels, e.g.
+ * to time them apart.  Errors: INVALID_ARG (also when D == 1), CUDA.
+ */
+int fdkod_backproject_decomposed(fdkod_plan_t *plan, const float *S, float *vol, uintptr_t stream);
+
+/*
+ * Recompute the plan's per-(square, view) bounds, shift centres and
+ * backprojection coefficients on the device (Eq. 1 at the vertices,
+ * FP64), asynchronously on `stream`, without allocating and without host
+ * synchronisation.  The plan computes them once at creation; this entry
+ * point exists so a pipeline step can include the bound stage.  The
+ * results are identical to the plan's.  Errors: INVALID_ARG, CUDA.
+ */
+int fdkod_compute_bounds(fdkod_plan_t *plan, uintptr_t stream);
+
+/*
  * Copy the plan's crop bounds to host arrays (each may be NULL):
  * lo, hi, crop [4^s][P] int32 (lo = floor(min u) and hi = floor(max u) + 1
  * over the square's four vertex voxel centres, so linear interpolation at

@@ -13,6 +13,8 @@ from .fdkod import (  # noqa: F401
     Plan,
     fdk_backproject_plain,
     fdkod_backproject,
+    fdkod_backproject_decomposed,
+    fdkod_compute_bounds,
     fdkod_decompose,
     fdkod_filter,
     fdkod_get_bounds,

@@ -289,6 +289,16 @@ int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t str
     return cuda_status(launch_decompose(plan->impl, Q, out, (cudaStream_t)stream));
 }
 
+int fdkod_backproject_decomposed(fdkod_plan_t *plan, const float *S, float *vol, uintptr_t stream) {
+    if (!plan || !S || !vol || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(launch_backproject(plan->impl, plan->impl.od, false, S, vol, (cudaStream_t)stream));
+}
+
+int fdkod_compute_bounds(fdkod_plan_t *plan, uintptr_t stream) {
+    if (!plan) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(launch_bounds(plan->impl, plan->impl.od, (cudaStream_t)stream));
+}
+
 int fdkod_get_bounds(const fdkod_plan_t *plan, int32_t *lo, int32_t *hi, int32_t *crop, double *phi,
                      int32_t *w0, int32_t *T) {
     if (!plan) return FDKOD_ERR_INVALID_ARG;

@@ -60,6 +60,8 @@ def load():
                 "fdkod_backproject": (i, [vp, vp, vp, u]),
                 "fdk_backproject_plain": (i, [vp, vp, vp, u]),
                 "fdkod_decompose": (i, [vp, vp, vp, u]),
+                "fdkod_backproject_decomposed": (i, [vp, vp, vp, u]),
+                "fdkod_compute_bounds": (i, [vp, u]),
                 "fdkod_get_bounds": (i, [vp, vp, vp, vp, vp, vp, vp]),
                 "fdkod_last_device_status": (i, [vp, u]),
                 "fdkod_strerror": (ctypes.c_char_p, [i]),
@@ -120,6 +122,15 @@ def fdk_backproject_plain(plan: int, Q, vol, stream=None) -> None:
 def fdkod_decompose(plan: int, Q, out, stream=None) -> None:
     _check(load().fdkod_decompose(plan, _dev_ptr(Q, "Q"), _dev_ptr(out, "out"), _stream(Q, stream)),
            "fdkod_decompose")
+
+
+def fdkod_backproject_decomposed(plan: int, S, vol, stream=None) -> None:
+    _check(load().fdkod_backproject_decomposed(plan, _dev_ptr(S, "S"), _dev_ptr(vol, "vol"), _stream(S, stream)),
+           "fdkod_backproject_decomposed")
+
+
+def fdkod_compute_bounds(plan: int, stream) -> None:
+    _check(load().fdkod_compute_bounds(plan, int(stream)), "fdkod_compute_bounds")
 
 
 def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
@@ -199,6 +210,15 @@ class Plan:
             out = torch.empty(shape, dtype=torch.float32, device=Q.device)
         fdkod_decompose(self.handle, Q, out, stream)
         return out
+
+    def backproject_decomposed(self, S, vol=None, stream=None):
+        vol = self._vol(S, vol)
+        fdkod_backproject_decomposed(self.handle, S, vol, stream)
+        return vol
+
+    def compute_bounds(self, stream=None):
+        import torch
+        fdkod_compute_bounds(self.handle, torch.cuda.current_stream().cuda_stream if stream is None else stream)
 
     def bounds(self) -> dict:
         return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)
