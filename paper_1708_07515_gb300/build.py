@@ -35,7 +35,7 @@ def nvcc() -> str:
 
 def _deps() -> list[str]:
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
-    return out + [os.path.join(INCLUDE, "fdkod.h")]
+    return out + [os.path.join(INCLUDE, "fdkod.h"), os.path.abspath(__file__)]
 
 
 def _stale(target: str, deps: list[str]) -> bool:

@@ -9,8 +9,11 @@
 #include <vector>
 
 #include "fdkod_internal.cuh"
+#include "tma.cuh"
 
 using namespace fdkod;
+
+#include <cudaTypedefs.h>
 
 namespace {
 
@@ -70,7 +73,8 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const std::vector<double2> &
     const int mside = (N + ss.m - 1) / ss.m;
     ss.tiles_per_side = (mside + kTile - 1) / kTile;
     double ext_t = 0.0, ext_v = 0.0;
-    const double zabs = 0.5 * (double)(N - 1);
+    // the last slab's tile may run kZT slices past the volume
+    const double zabs = 0.5 * (double)(N - 1) + kZT;
     for (int q = 0; q < ss.nsq; ++q) {
         int ix0, ix1, iy0, iy1;
         square_range(q % ss.m, ss.m, N, ix0, ix1);
@@ -105,6 +109,14 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const std::vector<double2> &
     ss.Wd = (int)ceil(ext_t) + 5;
     ss.Wd += ss.Wd & 1;  // even width: odd shared-memory row stride
     ss.Rw = (int)ceil(ext_v) + 5;
+    // TMA copies start on a 4-float boundary: up to 3 more columns
+    const int need = (int)ceil(ext_t) + 8;
+    ss.WdT = 0;
+    for (int w : {32, 48, 64, 96, 128})
+        if (need <= w) {
+            ss.WdT = w;
+            break;
+        }
 }
 
 int make_set(PlanImpl &p, SquareSet &ss, int s, cudaStream_t st, const std::vector<double2> &cs) {
@@ -201,9 +213,41 @@ int build_plan(PlanImpl &p, cudaStream_t st) {
     return FDKOD_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    return fn;
+}
+
 bool valid_dtype(int t) { return t == FDKOD_F32 || t == FDKOD_BF16 || t == FDKOD_F16; }
 
 }  // namespace
+
+namespace fdkod {
+
+cudaError_t encode_map_3d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, const uint64_t dims[3],
+                          const uint64_t strides[2], const uint32_t box[3]) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t gd[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gs[2] = {strides[0], strides[1]};
+    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(map, dt, 3, const_cast<void *>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace fdkod
 
 extern "C" {
 

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "fdkod_internal.cuh"
+#include "tma.cuh"
 
 namespace fdkod {
 namespace {
@@ -60,7 +61,7 @@ __device__ __forceinline__ void square_range(int q, int m, int N, int &i0, int &
 
 template <typename TS, bool DIRECT>
 __global__ void __launch_bounds__(kThreads)
-bp_kernel(BpParams a) {
+bp_generic_kernel(BpParams a) {
     extern __shared__ float win[];
     __shared__ float s_cb[kViewsPerChunk], s_sb[kViewsPerChunk], s_r[kViewsPerChunk], s_al[kViewsPerChunk],
         s_ga[kViewsPerChunk], s_g[kViewsPerChunk], s_toff[kViewsPerChunk], s_vrel[kViewsPerChunk];
@@ -108,7 +109,7 @@ bp_kernel(BpParams a) {
             const int k = j * a.vstep;
             const size_t o = (size_t)q * a.P + k;
             const GeomEntry ge = a.geo[o];
-            const float gf = (float)ge.g;
+            const float gf = ge.g_hi;
             const float toff = DIRECT ? ge.frac - (float)w0q : -(float)w0q;
             const int c = lane & 7;
             const float cx = (float)((c & 1) ? xe : x0) - half_n - xc;
@@ -118,7 +119,7 @@ bp_kernel(BpParams a) {
             const float invU = gf / fmaf(ge.r, dd, 1.0f);
             const float t = fmaf(invU, fmaf(ge.alpha, cx, ge.gamma * cy), toff);
             const float zq = zc * ge.r * dd;
-            const double vcen = fma((double)zc, ge.g, vcd);
+            const double vcen = fma((double)zc, (double)ge.g_hi + (double)ge.g_lo, vcd);
             const double v = vcen + (double)(invU * (cz - zq));
             float tmin = t, tmax = t;
             double vmin = v, vmax = v;
@@ -209,18 +210,290 @@ bp_kernel(BpParams a) {
 template <typename TS, bool DIRECT>
 cudaError_t launch_t(BpParams prm, int nsq, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)prm.J * prm.Rw * (prm.Wd + 1);
-    cudaError_t e = cudaFuncSetAttribute(bp_kernel<TS, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(bp_generic_kernel<TS, DIRECT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.N + kZT - 1) / kZT));
+    bp_generic_kernel<TS, DIRECT><<<grid, kThreads, smem, st>>>(prm);
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// TMA path.  Same tiling and arithmetic as the generic kernel, but each
+// view's window is one 3D bulk-tensor copy (zero fill outside the source),
+// two stages of kViewsPerStage views are in flight (copy of stage c+1
+// overlaps the gather of stage c), the per-view set-up is FP32 only, and the
+// inner loop is
+//   v = fma(1/U, i, v0);  m = v + 1.5*2^23 rounded down (= floor(v) in the
+//   low mantissa bits);  fv = v - (m - 1.5*2^23);  four shared loads at
+//   compile-time offsets;  two column lerps pre-weighted by U^-2;  row lerp.
+// Waits on the copies are bounded (FDKOD_ERR_TIMEOUT, then drain and exit).
+
+struct BpTmaParams {
+    float *vol;
+    const GeomEntry *geo;
+    const int32_t *crop;
+    const int32_t *w0;
+    int *status;
+    int N, P, Nv, m, tps;
+    int nviews, vstep, Pd;
+    int RW, tile_stride;  // window rows; floats per staged window (128-byte multiple)
+    float scale;
+};
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: integers sit in the low mantissa bits
+constexpr int kMagicBits = 0x4B400000;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+template <bool DIRECT, int WD>
+__global__ void __launch_bounds__(kThreads)
+bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned staging area (offset from the shared array itself so
+    // the compiler keeps shared-memory addressing)
+    float *sm = (float *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ float4 s_pa[2][kViewsPerStage];  // cos, sin, 1/d_c, alpha
+    __shared__ float4 s_pb[2][kViewsPerStage];  // gamma, g, column offset, row offset
+    __shared__ float s_zcr[2][kViewsPerStage];  // z_c / d_c
+    __shared__ int s_tx[2][kViewsPerStage], s_ty[2][kViewsPerStage], s_tz[2][kViewsPerStage];
+    __shared__ int s_skip[2][kViewsPerStage];
+
+    const int tiles = a.tps * a.tps;
+    const int q = blockIdx.x / tiles;
+    const int tt = blockIdx.x - q * tiles;
+    const int qy = q / a.m, qx = q - qy * a.m;
+    int ix0, ix1, iy0, iy1;
+    square_range(qx, a.m, a.N, ix0, ix1);
+    square_range(qy, a.m, a.N, iy0, iy1);
+    const int x0 = ix0 + (tt % a.tps) * kTile;
+    const int y0 = iy0 + (tt / a.tps) * kTile;
+    if (x0 > ix1 || y0 > iy1) return;  // ragged square: empty tile (uniform per CTA)
+    const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
+    const int z0 = blockIdx.y * kZT;
+    const int z1 = min(z0 + kZT - 1, a.N - 1);
+
+    const float half_n = 0.5f * (float)(a.N - 1);
+    const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;
+    const float yc = 0.5f * ((float)iy0 + (float)iy1) - half_n;
+    // centre of the full kZT-slice slab (also past the volume's end, so the
+    // window always covers every slice the loop evaluates)
+    const float zc = (float)z0 + 0.5f * (float)(kZT - 1) - half_n;
+    const float vcd = 0.5f * (float)(a.Nv - 1);
+
+    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool active = x <= xe && y <= ye;
+    const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t w0q = a.w0[q];
+    const int nch = (a.nviews + kViewsPerStage - 1) / kViewsPerStage;
+
+    // per-view window and coefficients of chunk c into stage st (warp w = view)
+    auto setup = [&](int c, int st) {
+        const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+        if (warp < nj) {
+            const int j = c * kViewsPerStage + warp;
+            const int k = j * a.vstep;
+            const size_t o = (size_t)q * a.P + k;
+            const GeomEntry ge = a.geo[o];
+            const int cbase = DIRECT ? a.crop[o] : 0;
+            const float toff = DIRECT ? ge.frac - (float)w0q : -(float)w0q;
+            const int cc = lane & 7;
+            const float cx = (float)((cc & 1) ? xe : x0) - half_n - xc;
+            const float cy = (float)((cc & 2) ? ye : y0) - half_n - yc;
+            const float cz = (cc & 4) ? 0.5f * (float)(kZT - 1) : -0.5f * (float)(kZT - 1);
+            const float dd = fmaf(ge.cb, cx, ge.sb * cy);
+            const float invU = __fdividef(ge.g_hi, fmaf(ge.r, dd, 1.0f));
+            const float t = fmaf(invU, fmaf(ge.alpha, cx, ge.gamma * cy), toff);
+            const float zcr = zc * ge.r;
+            // z_c g as hi + lo (exact product error by FMA)
+            const float ph = zc * ge.g_hi;
+            const float pl = fmaf(zc, ge.g_lo, fmaf(zc, ge.g_hi, -ph));
+            const float v = (ph + vcd) + (pl + invU * (cz - zcr * dd));
+            float tmin = t, tmax = t, vmin = v, vmax = v;
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) {
+                tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
+                tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+            }
+            if (lane == 0) {
+                // columns read: floor(t) .. floor(t) + 1 over the tile, with one
+                // sample of slack each side for FP32 rounding
+                const int clo = cbase + (int)floorf(tmin) - 1;
+                const int chi = cbase + (int)floorf(tmax) + 2;
+                const int xs = clo & ~3;  // 16-byte aligned start of the copy
+                const int vlo = (int)floorf(vmin) - 1;
+                const int vhi = (int)floorf(vmax) + 2;
+                const int skip = (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1);
+                if (skip) atomicOr(a.status, 1);
+                s_pa[st][warp] = make_float4(ge.cb, ge.sb, ge.r, ge.alpha);
+                s_pb[st][warp] = make_float4(ge.gamma, ge.g_hi, toff - (float)(xs - cbase),
+                                             (ph - ((float)vlo - vcd)) + pl);
+                s_zcr[st][warp] = zcr;
+                s_tx[st][warp] = xs;
+                s_ty[st][warp] = vlo;
+                s_tz[st][warp] = DIRECT ? k : q * a.Pd + j;
+                s_skip[st][warp] = skip;
+            }
+        }
+    };
+    auto issue = [&](int c, int st) {
+        const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+        tma::fence_proxy_async();
+        tma::mbar_arrive_expect_tx(&bars[st], (uint32_t)(nj * a.RW * WD * (int)sizeof(float)));
+        for (int w = 0; w < nj; ++w)
+            tma::load_3d(sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride, &tmap, &bars[st], s_tx[st][w],
+                         s_ty[st][w], s_tz[st][w]);
+    };
+
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
+        tma::fence_mbar_init();
+    }
+    __syncthreads();
+    setup(0, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) issue(0, 0);
+
+    float acc[kZT];
+#pragma unroll
+    for (int i = 0; i < kZT; ++i) acc[i] = 0.f;
+
+    for (int c = 0; c < nch; ++c) {
+        const int st = c & 1;
+        if (c + 1 < nch) setup(c + 1, st ^ 1);
+        __syncthreads();
+        if (c + 1 < nch && threadIdx.x == 0) issue(c + 1, st ^ 1);
+        const bool ok = tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+            // a copy never completed: report, let copies in flight land, leave
+            if (threadIdx.x == 0) atomicOr(a.status, 2);
+            tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+            if (c + 1 < nch) tma::mbar_wait_bounded(&bars[st ^ 1], (uint32_t)(((c + 1) >> 1) & 1), kWaitLimitNs);
+            return;
+        }
+        if (active) {
+            const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+            for (int w = 0; w < nj; ++w) {
+                if (s_skip[st][w]) continue;
+                const float4 pa = s_pa[st][w];
+                const float4 pb = s_pb[st][w];
+                const float dd = fmaf(pa.x, dx, pa.y * dy);
+                const float invU = __fdividef(pb.y, fmaf(pa.z, dd, 1.0f));
+                const float t = fmaf(invU, fmaf(pa.w, dx, pb.x * dy), pb.z);
+                const float tf = floorf(t);
+                const float wgt = invU * invU;
+                const float a1 = wgt * (t - tf);
+                const float a0 = wgt - a1;
+                const float vb0 = fmaf(invU, -0.5f * (float)(kZT - 1) - s_zcr[st][w] * dd, pb.w);
+                const float *tile = sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride + (int)tf;
+#pragma unroll
+                for (int i = 0; i < kZT; ++i) {
+                    const float v = fmaf(invU, (float)i, vb0);
+                    const float mg = __fadd_rd(v, kMagic);
+                    const float fv = v - (mg - kMagic);
+                    const float *p = tile + (__float_as_int(mg) - kMagicBits) * WD;
+                    const float c0 = fmaf(a1, p[1], a0 * p[0]);
+                    const float c1 = fmaf(a1, p[WD + 1], a0 * p[WD]);
+                    acc[i] = fmaf(fv, c1 - c0, acc[i] + c0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < kZT; ++i)
+            if (z0 + i <= z1) a.vol[((size_t)(z0 + i) * a.N + y) * a.N + x] = acc[i] * a.scale;
+    }
+}
+
+template <bool DIRECT, int WD>
+cudaError_t launch_tma_t(const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)2 * kViewsPerStage * prm.tile_stride + 128;
+    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<DIRECT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.N + kZT - 1) / kZT));
-    bp_kernel<TS, DIRECT><<<grid, kThreads, smem, st>>>(prm);
+    bp_tma_kernel<DIRECT, WD><<<grid, kThreads, smem, st>>>(map, prm);
     return cudaGetLastError();
+}
+
+template <bool DIRECT>
+cudaError_t launch_tma_w(int WD, const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
+    switch (WD) {
+        case 32: return launch_tma_t<DIRECT, 32>(map, prm, nsq, st);
+        case 48: return launch_tma_t<DIRECT, 48>(map, prm, nsq, st);
+        case 64: return launch_tma_t<DIRECT, 64>(map, prm, nsq, st);
+        case 96: return launch_tma_t<DIRECT, 96>(map, prm, nsq, st);
+        case 128: return launch_tma_t<DIRECT, 128>(map, prm, nsq, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The TMA path applies when the source is float32, 16-byte aligned, its
+// rows are whole 16-byte units, and the window fits a box (<= 256 rows).
+cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
+                           cudaStream_t st, bool &launched) {
+    launched = false;
+    if (ss.WdT == 0 || ss.Rw > 256 || ((uintptr_t)src & 15) != 0) return cudaSuccess;
+    if (direct && (p.qtype != FDKOD_F32 || (p.g.Nu % 4) != 0)) return cudaSuccess;
+    CUtensorMap map;
+    uint64_t dims[3], strides[2];
+    if (direct) {
+        dims[0] = (uint64_t)p.g.Nu;
+        dims[1] = (uint64_t)p.g.Nv;
+        dims[2] = (uint64_t)p.g.P;
+        strides[0] = (uint64_t)p.g.Nu * sizeof(float);
+    } else {
+        dims[0] = (uint64_t)p.Tstride;
+        dims[1] = (uint64_t)p.g.Nv;
+        dims[2] = (uint64_t)ss.nsq * p.Pd;
+        strides[0] = (uint64_t)p.Tstride * sizeof(float);
+    }
+    strides[1] = strides[0] * dims[1];
+    const uint32_t box[3] = {(uint32_t)ss.WdT, (uint32_t)ss.Rw, 1u};
+    cudaError_t e = encode_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src, dims, strides, box);
+    if (e != cudaSuccess) return cudaSuccess;  // not encodable: generic path
+    BpTmaParams a{};
+    a.vol = vol;
+    a.geo = ss.geo;
+    a.crop = ss.crop;
+    a.w0 = ss.w0;
+    a.status = p.status;
+    a.N = p.g.N;
+    a.P = p.g.P;
+    a.Nv = p.g.Nv;
+    a.m = ss.m;
+    a.tps = ss.tiles_per_side;
+    a.Pd = p.Pd;
+    a.RW = ss.Rw;
+    a.tile_stride = (ss.Rw * ss.WdT + 31) & ~31;
+    if (direct) {
+        a.nviews = p.g.P;
+        a.vstep = 1;
+        a.scale = (float)(M_PI / (double)p.g.P);
+    } else {
+        a.nviews = p.Pd;
+        a.vstep = p.D;
+        a.scale = (float)(M_PI / (double)p.Pd);
+    }
+    launched = true;
+    return direct ? launch_tma_w<true>(ss.WdT, map, a, ss.nsq, st) : launch_tma_w<false>(ss.WdT, map, a, ss.nsq, st);
 }
 
 }  // namespace
 
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
                                cudaStream_t st) {
+    bool launched = false;
+    cudaError_t te = try_launch_tma(p, ss, direct, src, vol, st, launched);
+    if (launched || te != cudaSuccess) return te;
     BpParams a{};
     a.src = src;
     a.vol = vol;

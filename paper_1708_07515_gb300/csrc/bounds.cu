@@ -103,7 +103,9 @@ bounds_kernel(double R, int N, int Nu, int P, int m, const double2 *__restrict__
         const double dc = R + xc * cb + yc * sb;
         const double e = (yc * cb - xc * sb) / dc;
         GeomEntry ge;
-        ge.g = R / dc;
+        const double g = R / dc;
+        ge.g_hi = (float)g;
+        ge.g_lo = (float)(g - (double)ge.g_hi);
         ge.cb = (float)cb;
         ge.sb = (float)sb;
         ge.r = (float)(1.0 / dc);

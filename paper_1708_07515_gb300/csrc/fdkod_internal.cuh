@@ -11,14 +11,15 @@ namespace fdkod {
 // Per-(square, view) backprojection geometry, from FP64 values computed by
 // the bound kernel.  With (dx, dy) a voxel's offset from the square centre
 // (x_c, y_c) and d_c = R + x_c cos b + y_c sin b:
-//   g = R / d_c (1/U at the centre, kept in FP64 for the row origin),
+//   g = R / d_c (1/U at the centre), stored as an unevaluated float pair
+//       g_hi + g_lo so the row origin z_c g keeps FP64-level accuracy,
 //   r = 1 / d_c,  e = a_c / R,  alpha = -sin b - e cos b,  gamma = cos b - e sin b,
 //   1/U = g / (1 + r (cb dx + sb dy)),
 //   a(x, y) - a(x_c, y_c) = (1/U) (alpha dx + gamma dy)      (Eq. 1 rearranged),
 // so the kernels work with small square-local numbers in FP32.
 // frac = (phi + w0) - floor(phi + w0), the sub-pixel part of the shift.
 struct GeomEntry {
-    double g;
+    float g_hi, g_lo;
     float cb, sb, r, alpha, gamma, frac;
 };
 static_assert(sizeof(GeomEntry) == 32, "GeomEntry layout");
@@ -32,14 +33,17 @@ struct SquareSet {
     GeomEntry *geo = nullptr;
     int32_t Tmax = 0;
     // staging window of the backprojection kernel (elements), from a host
-    // FP64 sweep over every tile and view
-    int Wd = 0, Rw = 0;
+    // FP64 sweep over every tile and view; WdT is the width of the TMA path
+    // (4-element alignment slack, rounded up to a kernel instantiation, 0
+    // when no instantiation is wide enough)
+    int Wd = 0, Rw = 0, WdT = 0;
     int tiles_per_side = 1;  // 16-voxel tiles per square side
 };
 
 constexpr int kTile = 16;      // tile side in x and y (threads per CTA = 256)
 constexpr int kZT = 16;        // z voxels per thread
-constexpr int kViewsPerChunk = 8;
+constexpr int kViewsPerChunk = 8;  // generic backprojection kernel
+constexpr int kViewsPerStage = 4;  // TMA backprojection kernel (two stages)
 
 struct PlanImpl {
     fdkod_geometry g{};
