@@ -93,7 +93,7 @@ typedef struct {
  * it with fdkod_destroy.  Errors: INVALID_ARG (null g/out, non-positive
  * sizes, R <= 0, unknown qtype), UNSUPPORTED (P % D != 0, s < 0,
  * s > 7, 2^s > N, R not beyond the volume, sizes above 2^15, Nu above
- * 8192), OOM, CUDA.
+ * 2048), OOM, CUDA.
  */
 int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out);
 

@@ -170,15 +170,15 @@ int make_fft_tables(PlanImpl &p, cudaStream_t st) {
         acc += ramlak(L / 2) * ctab[(size_t)((long long)k * (L / 2) % L)];
         H[k] = (float)(acc / (double)L);
     }
-    std::vector<float2> tw(L / 2);
-    for (int i = 0; i < L / 2; ++i) {
+    std::vector<float2> tw(L);
+    for (int i = 0; i < L; ++i) {
         const double a = 2.0 * M_PI * (double)i / (double)L;
         tw[i] = make_float2((float)cos(a), (float)(-sin(a)));
     }
     FDKOD_TRY(dalloc(p, &p.H, (size_t)L));
-    FDKOD_TRY(dalloc(p, &p.tw, (size_t)L / 2));
+    FDKOD_TRY(dalloc(p, &p.tw, (size_t)L));
     FDKOD_TRY(cudaMemcpyAsync(p.H, H.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
-    FDKOD_TRY(cudaMemcpyAsync(p.tw, tw.data(), sizeof(float2) * (L / 2), cudaMemcpyHostToDevice, st));
+    FDKOD_TRY(cudaMemcpyAsync(p.tw, tw.data(), sizeof(float2) * L, cudaMemcpyHostToDevice, st));
     FDKOD_TRY(cudaStreamSynchronize(st));
     return FDKOD_OK;
 }
@@ -258,8 +258,9 @@ int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_p
         return FDKOD_ERR_INVALID_ARG;
     const int lim = 1 << 15;
     if (g->N > lim || g->Nu > lim || g->Nv > lim || g->P > lim) return FDKOD_ERR_UNSUPPORTED;
-    // the filter's shared-memory FFT holds 2^ceil(log2(2 Nu)) complex floats
-    if (g->Nu > 8192) return FDKOD_ERR_UNSUPPORTED;
+    // the filter's shared-memory FFT holds two buffers of 2^ceil(log2(2 Nu))
+    // complex floats and uses one thread per 4 samples (at most 1024)
+    if (g->Nu > 2048) return FDKOD_ERR_UNSUPPORTED;
     if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0) return FDKOD_ERR_UNSUPPORTED;
     // the source must lie outside the volume's circumscribed cylinder
     if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;

@@ -55,7 +55,7 @@ struct PlanImpl {
     // filter stage
     int L = 0, log2L = 0;
     float *H = nullptr;        // ramp spectrum / L, real and even
-    float2 *tw = nullptr;      // e^{-2 pi i m / L}, m < L/2
+    float2 *tw = nullptr;      // e^{-2 pi i m / L}, m < L
     // decomposed data S'[q][j][v][t]
     float *Sp = nullptr;
     int Tstride = 0;

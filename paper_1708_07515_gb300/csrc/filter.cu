@@ -5,15 +5,20 @@
 // in the real part, row B in the imaginary part); the kernel's spectrum is
 // real and even, so after the pointwise product the inverse transform
 // returns filtered A in the real part and filtered B in the imaginary part.
+// The transforms are radix-4 Stockham passes (plus one radix-2 pass when
+// log2 L is odd) between two shared-memory buffers, one CTA of L/4 threads
+// per row pair; the twiddle table holds e^{-2 pi i m / L} for m < L.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <algorithm>
 
 #include "fdkod_internal.cuh"
 
 namespace fdkod {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 
 template <typename T>
 __device__ __forceinline__ T to_q(float x);
@@ -28,11 +33,70 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// One Stockham pass (natural-order input and output, ping-pong buffers):
+// item j reads R samples j + r L/R, twiddles them by e^{-2 pi i r (j mod Ns) / (Ns R)},
+// does an R-point DFT and writes them to (j / Ns) Ns R + (j mod Ns) + r Ns.
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                              const float2 *__restrict__ tw, int L, int Ns) {
+    const int n_items = L / R;
+    const int tstep = L / (Ns * R);
+    for (int j = threadIdx.x; j < n_items; j += blockDim.x) {
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[j + r * n_items];
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tstep]);
+        if (R == 4) {
+            const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+            const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+            const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+            const float2 d13 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
+            v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            // -i * d13 = (d13.y, -d13.x)
+            v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);
+            v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);
+        } else {
+            const float2 a = v[0], b = v[1];
+            v[0] = make_float2(a.x + b.x, a.y + b.y);
+            v[1] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[d + r * Ns] = v[r];
+    }
+}
+
+// Forward DFT of length L = 2^log2L held in a; returns the buffer holding
+// the result (a or b).
+__device__ __forceinline__ float2 *fft_forward(float2 *a, float2 *b, const float2 *tw, int L, int log2L) {
+    int Ns = 1;
+    for (int p = 0; p + 2 <= log2L; p += 2) {
+        stockham_pass<4>(a, b, tw, L, Ns);
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+        Ns *= 4;
+    }
+    if (log2L & 1) {
+        stockham_pass<2>(a, b, tw, L, Ns);
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
               const float2 *__restrict__ tw, int L, int log2L, int Nu, int Nv, long long nrows, float R) {
     extern __shared__ float2 z[];
+    float2 *a = z, *b = z + L;
     const long long rowA = 2LL * blockIdx.x;
     const long long rowB = rowA + 1;
     const bool hasB = rowB < nrows;
@@ -41,58 +105,32 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
     const float bA = (float)(rowA % Nv) - 0.5f * (float)(Nv - 1);
     const float bB = (float)(rowB % Nv) - 0.5f * (float)(Nv - 1);
     const float R2 = R * R;
-    const int sh = 32 - log2L;
-    // weighted rows, loaded in bit-reversed order for the decimation-in-time pass
-    for (int i = threadIdx.x; i < L; i += kThreads) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
         float2 v = make_float2(0.f, 0.f);
         if (i < Nu) {
-            const float a = (float)i - 0.5f * (float)(Nu - 1);
-            v.x = __ldg(pA + i) * (R / sqrtf(R2 + a * a + bA * bA));
-            if (hasB) v.y = __ldg(pB + i) * (R / sqrtf(R2 + a * a + bB * bB));
+            const float u = (float)i - 0.5f * (float)(Nu - 1);
+            v.x = __ldg(pA + i) * (R / sqrtf(R2 + u * u + bA * bA));
+            if (hasB) v.y = __ldg(pB + i) * (R / sqrtf(R2 + u * u + bB * bB));
         }
-        z[__brev((unsigned)i) >> sh] = v;
+        a[i] = v;
     }
     __syncthreads();
-    const int half_n = L >> 1;
-    // forward transform, decimation in time: natural-order output
-    for (int half = 1, tstep = half_n; half < L; half <<= 1, tstep >>= 1) {
-        for (int b = threadIdx.x; b < half_n; b += kThreads) {
-            const int pos = b & (half - 1);
-            const int i = ((b - pos) << 1) + pos;
-            const int j = i + half;
-            const float2 t = cmul(tw[pos * tstep], z[j]);
-            const float2 a = z[i];
-            z[i] = make_float2(a.x + t.x, a.y + t.y);
-            z[j] = make_float2(a.x - t.x, a.y - t.y);
-        }
-        __syncthreads();
-    }
-    // pointwise product with the (real, even) ramp spectrum, 1/L folded in
-    for (int i = threadIdx.x; i < L; i += kThreads) {
+    float2 *x = fft_forward(a, b, tw, L, log2L);
+    // product with the real, even ramp spectrum (1/L folded in), conjugated:
+    // the inverse transform is the conjugate of a forward transform
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const float h = H[i];
-        const float2 v = z[i];
-        z[i] = make_float2(v.x * h, v.y * h);
+        const float2 v = x[i];
+        x[i] = make_float2(v.x * h, -v.y * h);
     }
     __syncthreads();
-    // inverse transform, decimation in frequency: bit-reversed output
-    for (int half = half_n, tstep = 1; half >= 1; half >>= 1, tstep <<= 1) {
-        for (int b = threadIdx.x; b < half_n; b += kThreads) {
-            const int pos = b & (half - 1);
-            const int i = ((b - pos) << 1) + pos;
-            const int j = i + half;
-            const float2 a = z[i], c = z[j];
-            const float2 w = tw[pos * tstep];
-            z[i] = make_float2(a.x + c.x, a.y + c.y);
-            z[j] = cmul(make_float2(a.x - c.x, a.y - c.y), make_float2(w.x, -w.y));
-        }
-        __syncthreads();
-    }
+    float2 *y = fft_forward(x, x == a ? b : a, tw, L, log2L);
     TQ *qA = Q + rowA * Nu;
     TQ *qB = Q + rowB * Nu;
-    for (int u = threadIdx.x; u < Nu; u += kThreads) {
-        const float2 v = z[__brev((unsigned)u) >> sh];
+    for (int u = threadIdx.x; u < Nu; u += blockDim.x) {
+        const float2 v = y[u];
         qA[u] = to_q<TQ>(v.x);
-        if (hasB) qB[u] = to_q<TQ>(v.y);
+        if (hasB) qB[u] = to_q<TQ>(-v.y);
     }
 }
 
@@ -100,12 +138,13 @@ template <typename TQ>
 cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st) {
     const long long nrows = (long long)p.g.P * p.g.Nv;
     const long long blocks = (nrows + 1) / 2;
-    const size_t smem = sizeof(float2) * (size_t)p.L;
+    const size_t smem = 2 * sizeof(float2) * (size_t)p.L;
     cudaError_t e = cudaFuncSetAttribute(filter_kernel<TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    filter_kernel<TQ><<<(unsigned)blocks, kThreads, smem, st>>>(proj, Q, p.H, p.tw, p.L, p.log2L, p.g.Nu,
-                                                                p.g.Nv, nrows, (float)p.g.R);
+    const int threads = std::max(32, std::min(kThreads, p.L / 4));
+    filter_kernel<TQ><<<(unsigned)blocks, threads, smem, st>>>(proj, Q, p.H, p.tw, p.L, p.log2L, p.g.Nu,
+                                                               p.g.Nv, nrows, (float)p.g.R);
     return cudaGetLastError();
 }
 
