@@ -184,6 +184,41 @@ int fdkod_get_bounds(const fdkod_plan_t *plan, int32_t *lo, int32_t *hi, int32_t
  */
 int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
 
+/*
+ * FDK-OD backprojection that allocates nothing.  The paper has no
+ * counterpart: this is a deployment variant of fdkod_backproject.
+ *
+ * For callers that cannot call cudaMalloc, e.g. an acquisition pipeline
+ * that fixes its device memory at start-up and forbids allocation later
+ * (cudaMalloc may synchronise the device and its latency is unbounded), or
+ * a host application whose own memory pool has already reserved the
+ * device, so an extra cudaMalloc would fail.  It needs no plan: it computes
+ * the bounds, the decomposed data and the volume of fdkod_plan(g, s, D,
+ * FDKOD_F32) + fdkod_backproject in one call, with the same kernels.
+ *
+ * Working memory: one file-scope device array of 48 MiB inside libfdkod,
+ * which every GPU that loads the library holds until the process exits.
+ * A call needs 52 bytes per (square, view) pair plus 4 * 4^s * (P/D) * Nv
+ * * T_stride bytes of decomposed data (T_stride ~ 1.4 N/2^s + 8) plus a few
+ * KiB; larger problems return FDKOD_ERR_UNSUPPORTED without touching the
+ * GPU.  Example: 128^3 from 128 views, s = 2, D = 2 needs about 30 MiB.
+ * The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * previous call's contents: the call clears what must start at zero, but
+ * calls whose work overlaps on the GPU (other streams, other host threads
+ * without ordering) race on it -- order them on one stream.  Host callers
+ * are serialised by a mutex.  Device-side window checks are sized out on
+ * the host and are not reported by this call.
+ *
+ * g, s, D: as fdkod_plan; Q: device [P][Nv][Nu] float32 (already
+ * filtered); vol: device [N][N][N] float32, fully overwritten; work is
+ * enqueued on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (as fdkod_plan,
+ * P > 8192, or over the 48 MiB limit), CUDA.
+ */
+int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, const float *Q, float *vol,
+                              uintptr_t stream);
+
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);
 

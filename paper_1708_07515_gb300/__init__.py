@@ -14,6 +14,7 @@ from .fdkod import (  # noqa: F401
     fdk_backproject_plain,
     fdkod_backproject,
     fdkod_backproject_decomposed,
+    fdkod_backproject_noalloc,
     fdkod_compute_bounds,
     fdkod_decompose,
     fdkod_filter,

@@ -63,11 +63,15 @@ void square_range(int q, int m, int N, int &i0, int &i1) {
     i1 = (int)((((long long)q + 1) * N + m - 1) / m) - 1;
 }
 
+}  // namespace
+
+namespace fdkod {
+
 // Staging window of the backprojection kernel: the largest column and row
 // extent any 16 x 16 x kZT voxel tile of this square set can touch in one
 // view, from an FP64 sweep over all tiles and views (column coordinate
 // relative to the square centre; row extent bounded over all slabs).
-void size_windows(const PlanImpl &p, SquareSet &ss, const std::vector<double2> &cs) {
+void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     const double R = p.g.R;
     const int N = p.g.N, P = p.g.P;
     const int mside = (N + ss.m - 1) / ss.m;
@@ -119,6 +123,10 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const std::vector<double2> &
         }
 }
 
+}  // namespace fdkod
+
+namespace {
+
 int make_set(PlanImpl &p, SquareSet &ss, int s, cudaStream_t st, const std::vector<double2> &cs) {
     ss.s = s;
     ss.m = 1 << s;
@@ -136,7 +144,7 @@ int make_set(PlanImpl &p, SquareSet &ss, int s, cudaStream_t st, const std::vect
     FDKOD_TRY(cudaMemcpyAsync(T.data(), ss.T, sizeof(int32_t) * ss.nsq, cudaMemcpyDeviceToHost, st));
     FDKOD_TRY(cudaStreamSynchronize(st));
     ss.Tmax = *std::max_element(T.begin(), T.end());
-    size_windows(p, ss, cs);
+    size_windows(p, ss, cs.data());
     return FDKOD_OK;
 }
 

@@ -64,6 +64,9 @@ struct PlanImpl {
     int64_t device_bytes = 0;
 };
 
+// host: backprojection staging windows of a square set (cs = cos/sin per view)
+void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs);
+
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_bounds(const PlanImpl &p, SquareSet &ss, cudaStream_t st);
 cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st);

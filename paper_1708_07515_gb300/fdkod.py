@@ -62,6 +62,7 @@ def load():
                 "fdkod_decompose": (i, [vp, vp, vp, u]),
                 "fdkod_backproject_decomposed": (i, [vp, vp, vp, u]),
                 "fdkod_compute_bounds": (i, [vp, u]),
+                "fdkod_backproject_noalloc": (i, [ctypes.POINTER(Geometry), i, i, vp, vp, u]),
                 "fdkod_get_bounds": (i, [vp, vp, vp, vp, vp, vp, vp]),
                 "fdkod_last_device_status": (i, [vp, u]),
                 "fdkod_strerror": (ctypes.c_char_p, [i]),
@@ -131,6 +132,15 @@ def fdkod_backproject_decomposed(plan: int, S, vol, stream=None) -> None:
 
 def fdkod_compute_bounds(plan: int, stream) -> None:
     _check(load().fdkod_compute_bounds(plan, int(stream)), "fdkod_compute_bounds")
+
+
+def fdkod_backproject_noalloc(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, Q, vol,
+                              stream=None) -> None:
+    """FDK-OD backprojection without any allocation (scratch in the library's
+    fixed device array); Q float32 [P][Nv][Nu], vol float32 [N][N][N]."""
+    g = Geometry(float(R), int(N), int(Nu), int(Nv), int(P))
+    _check(load().fdkod_backproject_noalloc(ctypes.byref(g), int(s), int(D), _dev_ptr(Q, "Q"), _dev_ptr(vol, "vol"),
+                                            _stream(Q, stream)), "fdkod_backproject_noalloc")
 
 
 def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
