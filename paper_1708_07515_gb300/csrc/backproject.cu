@@ -242,6 +242,14 @@ struct BpTmaParams {
     float scale;
 };
 
+// shared-memory load at a compile-time byte offset from a 32-bit address
+template <int OFF>
+__device__ __forceinline__ float lds(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF) : "memory");
+    return v;
+}
+
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: integers sit in the low mantissa bits
 constexpr int kMagicBits = 0x4B400000;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
@@ -253,6 +261,7 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     // 128-byte aligned staging area (offset from the shared array itself so
     // the compiler keeps shared-memory addressing)
     float *sm = (float *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    const uint32_t sbase = tma::smem_u32(sm);
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ float4 s_pa[2][kViewsPerStage];  // cos, sin, 1/d_c, alpha
     __shared__ float4 s_pb[2][kViewsPerStage];  // gamma, g, column offset, row offset
@@ -391,15 +400,19 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
                 const float a1 = wgt * (t - tf);
                 const float a0 = wgt - a1;
                 const float vb0 = fmaf(invU, -0.5f * (float)(kZT - 1) - s_zcr[st][w] * dd, pb.w);
-                const float *tile = sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride + (int)tf;
+                // 32-bit shared address of sample (row 0, column floor(t)),
+                // pre-offset so that the magic-number bits index the row
+                const uint32_t tbase = sbase + 4u * ((uint32_t)(st * kViewsPerStage + w) * (uint32_t)a.tile_stride +
+                                                     (uint32_t)(int)tf) -
+                                       (uint32_t)kMagicBits * (uint32_t)(4 * WD);
 #pragma unroll
                 for (int i = 0; i < kZT; ++i) {
                     const float v = fmaf(invU, (float)i, vb0);
                     const float mg = __fadd_rd(v, kMagic);
                     const float fv = v - (mg - kMagic);
-                    const float *p = tile + (__float_as_int(mg) - kMagicBits) * WD;
-                    const float c0 = fmaf(a1, p[1], a0 * p[0]);
-                    const float c1 = fmaf(a1, p[WD + 1], a0 * p[WD]);
+                    const uint32_t ad = (uint32_t)__float_as_int(mg) * (uint32_t)(4 * WD) + tbase;
+                    const float c0 = fmaf(a1, lds<4>(ad), a0 * lds<0>(ad));
+                    const float c1 = fmaf(a1, lds<4 * WD + 4>(ad), a0 * lds<4 * WD>(ad));
                     acc[i] = fmaf(fv, c1 - c0, acc[i] + c0);
                 }
             }

@@ -153,6 +153,11 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     const size_t vstride = (size_t)Nv * Tstride;
     float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride;
     const bool vok = v < Nv;
+    bool valid[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) valid[i] = tx + 32 * i < T;
+    // the stream starts at k' = -(D-1): block j0 = -1, tap r = 1 (D > 1)
+    int j0 = D > 1 ? -1 : 0, r = D > 1 ? 1 : 0;
 
     for (int n = 0; n < nstage; ++n) {
         const int slot = n % kStages;
@@ -164,45 +169,41 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                 tma::mbar_wait_bounded(&bars[m % kStages], (uint32_t)((m / kStages) & 1), kDecWaitNs);
             return;
         }
-        const int base = n * kG;
-        const int nv = min(kG, nstream - base);
+        const int nv = min(kG, nstream - n * kG);
         for (int w = 0; w < nv; ++w) {
-            const int kp = base + w - (D - 1);       // stream position -> k'
-            const int j0 = kp < 0 ? -1 : kp / D;     // decimated view the sample starts
-            const int r = kp - j0 * D;               // 0..D-1
+            // stream position -> decimated view j0 (-1 for the wrapped block)
+            // and tap r, advanced incrementally (no division)
             const TQ *row = sm + (size_t)(slot * kG + w) * tile_stride + (size_t)ty * Wc + s_off[slot][w] + tx;
             const float f = s_f[slot][w];
-            const float wa = (float)(D - r), wb = (float)r;
+            const float wa = j0 >= 0 ? (float)(D - r) : 0.f, wb = (float)r;
 #pragma unroll
             for (int i = 0; i < NT; ++i) {
                 // columns t < T read at most T + 3 < Wc elements into the row
-                if (tx + 32 * i < T) {
+                if (valid[i]) {
                     const float a0 = sm_ld(row + 32 * i), a1 = sm_ld(row + 32 * i + 1);
                     const float smp = fmaf(f, a1 - a0, a0);
-                    if (j0 >= 0) cur[i] = fmaf(wa, smp, cur[i]);
+                    cur[i] = fmaf(wa, smp, cur[i]);
                     nxt[i] = fmaf(wb, smp, nxt[i]);
                 }
             }
-            if (j0 < 0 && r == D - 1) {
-                // the wrapped block only seeds decimated view 0
-#pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    cur[i] = nxt[i];
-                    nxt[i] = 0.f;
-                }
-            } else if (j0 >= 0 && r == D - 1) {
-                if (vok) {
+            if (r == D - 1) {
+                if (j0 >= 0 && vok) {
 #pragma unroll
                     for (int i = 0; i < NT; ++i) {
                         const int t = tx + 32 * i;
                         if (t < Tstride) out[(size_t)j0 * vstride + t] = t < T ? cur[i] * inv : 0.f;
                     }
                 }
+                // the wrapped block (j0 = -1) only seeds decimated view 0
 #pragma unroll
                 for (int i = 0; i < NT; ++i) {
                     cur[i] = nxt[i];
                     nxt[i] = 0.f;
                 }
+                r = 0;
+                ++j0;
+            } else {
+                ++r;
             }
         }
         __syncthreads();

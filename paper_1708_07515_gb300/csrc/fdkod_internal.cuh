@@ -41,7 +41,7 @@ struct SquareSet {
 };
 
 constexpr int kTile = 16;      // tile side in x and y (threads per CTA = 256)
-constexpr int kZT = 16;        // z voxels per thread
+constexpr int kZT = 32;        // z voxels per thread
 constexpr int kViewsPerChunk = 8;  // generic backprojection kernel
 constexpr int kViewsPerStage = 4;  // TMA backprojection kernel (two stages)
 
