@@ -161,9 +161,9 @@ int make_fft_tables(PlanImpl &p, cudaStream_t st) {
         L <<= 1;
         ++lg;
     }
-    if (L < 4) {
-        L = 4;
-        lg = 2;
+    if (L < 16) {  // the filter's transforms start with a radix-16 pass
+        L = 16;
+        lg = 4;
     }
     p.L = L;
     p.log2L = lg;

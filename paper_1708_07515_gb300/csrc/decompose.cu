@@ -97,6 +97,9 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                      int tile_stride) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TQ *sm = (TQ *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    // per-view tables after the staging ring
+    int *s_crop = (int *)((unsigned char *)sm + sizeof(TQ) * (size_t)kStages * kG * tile_stride);
+    float *s_frac = (float *)(s_crop + P);
     __shared__ __align__(8) uint64_t bars[kStages];
     __shared__ int s_off[kStages][kG];
     __shared__ float s_f[kStages][kG];
@@ -119,11 +122,10 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
         if (tx < nv) {
             const int kp = base + tx - (D - 1);
             kk = kp < 0 ? kp + P : kp;
-            const size_t o = (size_t)q * P + kk;
-            const int c = crop[o];
+            const int c = s_crop[kk];
             xs = c & ~(kAlign - 1);
             s_off[slot][tx] = c - xs;
-            s_f[slot][tx] = geo[o].frac;
+            s_f[slot][tx] = s_frac[kk];
         }
         __syncwarp();
         if (tx == 0) {
@@ -138,6 +140,11 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
         }
     };
 
+    // this square's crop columns and shift fractions, once per CTA
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        s_crop[k] = crop[(size_t)q * P + k];
+        s_frac[k] = geo[(size_t)q * P + k].frac;
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) tma::mbar_init(&bars[i], 1);
         tma::fence_mbar_init();
@@ -213,7 +220,7 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
 template <typename TQ, int NT>
 cudaError_t launch_tma_nt(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st) {
     const int tile_stride = (kVB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
-    const size_t smem = sizeof(TQ) * (size_t)kStages * kG * tile_stride + 128;
+    const size_t smem = sizeof(TQ) * (size_t)kStages * kG * tile_stride + 128 + 8 * (size_t)p.g.P;
     cudaError_t e = cudaFuncSetAttribute(decompose_tma_kernel<TQ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -231,7 +238,7 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     constexpr int kAlign = 16 / (int)sizeof(TQ);
     if ((p.g.Nu % kAlign) != 0 || ((uintptr_t)Q & 15) != 0) return cudaSuccess;
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
-    if (Wc > 256 || p.Tstride > 256) return cudaSuccess;
+    if (Wc > 256 || p.Tstride > 256 || p.g.P > 4096) return cudaSuccess;
     CUtensorMap map;
     const uint64_t dims[3] = {(uint64_t)p.g.Nu, (uint64_t)p.g.Nv, (uint64_t)p.g.P};
     const uint64_t strides[2] = {(uint64_t)p.g.Nu * sizeof(TQ), (uint64_t)p.g.Nu * p.g.Nv * sizeof(TQ)};

@@ -5,9 +5,9 @@
 // in the real part, row B in the imaginary part); the kernel's spectrum is
 // real and even, so after the pointwise product the inverse transform
 // returns filtered A in the real part and filtered B in the imaginary part.
-// The transforms are radix-4 Stockham passes (plus one radix-2 pass when
-// log2 L is odd) between two shared-memory buffers, one CTA of L/4 threads
-// per row pair; the twiddle table holds e^{-2 pi i m / L} for m < L.
+// The transforms are in-place Stockham passes of radix 16 (16-point DFTs in
+// registers) plus one pass of radix 2, 4 or 8; L/16 threads per row pair and
+// several pairs per CTA; the twiddle table holds e^{-2 pi i m / L}, m < L.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -33,118 +33,199 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// One Stockham pass (natural-order input and output, ping-pong buffers):
-// item j reads R samples j + r L/R, twiddles them by e^{-2 pi i r (j mod Ns) / (Ns R)},
-// does an R-point DFT and writes them to (j / Ns) Ns R + (j mod Ns) + r Ns.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i
+__device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
+
+// 4-point forward DFT in place: (a, b, c, d) -> (X0, X1, X2, X3)
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 s02 = cadd(a, c), d02 = csub(a, c), s13 = cadd(b, d), d13 = csub(b, d);
+    a = cadd(s02, s13);
+    c = csub(s02, s13);
+    b = cadd(d02, cmi(d13));
+    d = csub(d02, cmi(d13));
+}
+
+constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
+constexpr float kS1 = 0.38268343236508978f;  // sin(pi/8)
+constexpr float kH = 0.70710678118654752f;   // cos(pi/4)
+
+// R-point forward DFT of v in registers; result X[k] left at v[pos(k)]
+// with pos(k) = (R/4) (k mod 4) + k / 4 for R = 16 and 2 (k mod 4) + k / 4
+// for R = 8 (the 4 x R/4 index map); R = 4, 2: natural order.
 template <int R>
-__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                              const float2 *__restrict__ tw, int L, int Ns) {
+__device__ __forceinline__ void dft(float2 *v);
+
+template <>
+__device__ __forceinline__ void dft<2>(float2 *v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void dft<4>(float2 *v) { dft4(v[0], v[1], v[2], v[3]); }
+
+template <>
+__device__ __forceinline__ void dft<8>(float2 *v) {
+    // n = 2 n1 + n2: 4-point DFTs over n1, twiddle W8^(n2 k1), 2-point over n2
+    dft4(v[0], v[2], v[4], v[6]);
+    dft4(v[1], v[3], v[5], v[7]);
+    v[3] = cmul(v[3], make_float2(kH, -kH));
+    v[5] = cmi(v[5]);
+    v[7] = cmul(v[7], make_float2(-kH, -kH));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        const float2 a = v[2 * k1], b = v[2 * k1 + 1];
+        v[2 * k1] = cadd(a, b);
+        v[2 * k1 + 1] = csub(a, b);
+    }
+}
+
+template <>
+__device__ __forceinline__ void dft<16>(float2 *v) {
+    // n = 4 n1 + n2: 4-point DFTs over n1, twiddle W16^(n2 k1), 4-point over n2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // position n2 + 4 k1 holds Y[n2][k1]
+    v[1 + 4 * 1] = cmul(v[1 + 4 * 1], make_float2(kC1, -kS1));   // W16^1
+    v[1 + 4 * 2] = cmul(v[1 + 4 * 2], make_float2(kH, -kH));     // W16^2
+    v[1 + 4 * 3] = cmul(v[1 + 4 * 3], make_float2(kS1, -kC1));   // W16^3
+    v[2 + 4 * 1] = cmul(v[2 + 4 * 1], make_float2(kH, -kH));     // W16^2
+    v[2 + 4 * 2] = cmi(v[2 + 4 * 2]);                            // W16^4
+    v[2 + 4 * 3] = cmul(v[2 + 4 * 3], make_float2(-kH, -kH));    // W16^6
+    v[3 + 4 * 1] = cmul(v[3 + 4 * 1], make_float2(kS1, -kC1));   // W16^3
+    v[3 + 4 * 2] = cmul(v[3 + 4 * 2], make_float2(-kH, -kH));    // W16^6
+    v[3 + 4 * 3] = cmul(v[3 + 4 * 3], make_float2(-kC1, kS1));   // W16^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+}
+
+template <int R>
+__device__ __forceinline__ constexpr int out_pos(int k) {
+    return R == 16 ? 4 * (k % 4) + k / 4 : (R == 8 ? 2 * (k % 4) + k / 4 : k);
+}
+
+// shared-memory index with one pad slot per 16 (breaks stride-16 conflicts)
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+// One in-place Stockham pass of radix R over a buffer of length L (padded):
+// item j reads R samples j + r L/R, twiddles them by
+// e^{-2 pi i r (j mod Ns) / (Ns R)}, does an R-point DFT and writes sample
+// r to (j - j mod Ns) R + (j mod Ns) + r Ns.  Each thread owns 16/R items
+// (16 values), all loaded before the barrier that precedes the stores.
+template <int R>
+__device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int L, int Ns, int lt, int nt) {
+    constexpr int kItems = 16 / R;
     const int n_items = L / R;
     const int tstep = L / (Ns * R);
-    for (int j = threadIdx.x; j < n_items; j += blockDim.x) {
+    float2 v[kItems][R];
+    int dst[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int j = lt + it * nt;
         const int k = j % Ns;
-        float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[j + r * n_items];
+        for (int r = 0; r < R; ++r) v[it][r] = buf[pad(j + r * n_items)];
+        if (Ns > 1) {
+            float2 w[R];
+            w[1] = tw[k * tstep];
+            if (R >= 4) w[2] = tw[2 * k * tstep];
+            if (R >= 4) w[3] = cmul(w[1], w[2]);
+            if (R >= 8) {
+                w[4] = tw[4 * k * tstep];
+                w[5] = cmul(w[1], w[4]);
+                w[6] = cmul(w[2], w[4]);
+                w[7] = cmul(w[3], w[4]);
+            }
+            if (R >= 16) {
+                w[8] = tw[8 * k * tstep];
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tstep]);
-        if (R == 4) {
-            const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-            const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-            const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-            const float2 d13 = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-            v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
-            v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
-            // -i * d13 = (d13.y, -d13.x)
-            v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);
-            v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);
-        } else {
-            const float2 a = v[0], b = v[1];
-            v[0] = make_float2(a.x + b.x, a.y + b.y);
-            v[1] = make_float2(a.x - b.x, a.y - b.y);
+                for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+            }
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
         }
-        const int d = (j - k) * R + k;
+        dft<R>(v[it]);
+        dst[it] = (j - k) * R + k;
+    }
+    __syncthreads();
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[d + r * Ns] = v[r];
-    }
+    for (int it = 0; it < kItems; ++it)
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad(dst[it] + r * Ns)] = v[it][out_pos<R>(r)];
+    __syncthreads();
 }
 
-// Forward DFT of length L = 2^log2L held in a; returns the buffer holding
-// the result (a or b).
-__device__ __forceinline__ float2 *fft_forward(float2 *a, float2 *b, const float2 *tw, int L, int log2L) {
+// Forward DFT of length L = 2^log2L (>= 16) in place: radix-16 passes, then
+// one pass of radix 2, 4 or 8 for the remaining factor.
+__device__ __forceinline__ void fft_forward(float2 *buf, const float2 *tw, int L, int lt, int nt) {
     int Ns = 1;
-    for (int p = 0; p + 2 <= log2L; p += 2) {
-        stockham_pass<4>(a, b, tw, L, Ns);
-        __syncthreads();
-        float2 *t = a;
-        a = b;
-        b = t;
-        Ns *= 4;
+    while (Ns * 16 <= L) {
+        pass<16>(buf, tw, L, Ns, lt, nt);
+        Ns *= 16;
     }
-    if (log2L & 1) {
-        stockham_pass<2>(a, b, tw, L, Ns);
-        __syncthreads();
-        float2 *t = a;
-        a = b;
-        b = t;
-    }
-    return a;
+    const int rest = L / Ns;
+    if (rest == 8) pass<8>(buf, tw, L, Ns, lt, nt);
+    else if (rest == 4) pass<4>(buf, tw, L, Ns, lt, nt);
+    else if (rest == 2) pass<2>(buf, tw, L, Ns, lt, nt);
 }
 
+// G row pairs per CTA, L/16 threads per pair.
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
-              const float2 *__restrict__ tw, int L, int log2L, int Nu, int Nv, long long nrows, float R) {
+              const float2 *__restrict__ tw, int L, int G, int Nu, int Nv, long long nrows, float R) {
     extern __shared__ float2 z[];
-    float2 *a = z, *b = z + L;
-    const long long rowA = 2LL * blockIdx.x;
+    const int nt = L / 16;
+    const int g = threadIdx.x / nt, lt = threadIdx.x % nt;
+    float2 *buf = z + (size_t)g * (L + L / 16);
+    const long long rowA = 2LL * ((long long)blockIdx.x * G + g);
     const long long rowB = rowA + 1;
-    const bool hasB = rowB < nrows;
-    const float *pA = proj + rowA * Nu;
-    const float *pB = proj + rowB * Nu;
+    const bool hasA = rowA < nrows, hasB = rowB < nrows;
     const float bA = (float)(rowA % Nv) - 0.5f * (float)(Nv - 1);
     const float bB = (float)(rowB % Nv) - 0.5f * (float)(Nv - 1);
     const float R2 = R * R;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    for (int i = lt; i < L; i += nt) {
         float2 v = make_float2(0.f, 0.f);
         if (i < Nu) {
             const float u = (float)i - 0.5f * (float)(Nu - 1);
-            v.x = __ldg(pA + i) * (R / sqrtf(R2 + u * u + bA * bA));
-            if (hasB) v.y = __ldg(pB + i) * (R / sqrtf(R2 + u * u + bB * bB));
+            if (hasA) v.x = __ldg(proj + rowA * Nu + i) * (R * rsqrtf(R2 + u * u + bA * bA));
+            if (hasB) v.y = __ldg(proj + rowB * Nu + i) * (R * rsqrtf(R2 + u * u + bB * bB));
         }
-        a[i] = v;
+        buf[pad(i)] = v;
     }
     __syncthreads();
-    float2 *x = fft_forward(a, b, tw, L, log2L);
+    fft_forward(buf, tw, L, lt, nt);
     // product with the real, even ramp spectrum (1/L folded in), conjugated:
     // the inverse transform is the conjugate of a forward transform
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const float h = H[i];
-        const float2 v = x[i];
-        x[i] = make_float2(v.x * h, -v.y * h);
+    for (int i = lt; i < L; i += nt) {
+        const float h = __ldg(H + i);
+        const float2 v = buf[pad(i)];
+        buf[pad(i)] = make_float2(v.x * h, -v.y * h);
     }
     __syncthreads();
-    float2 *y = fft_forward(x, x == a ? b : a, tw, L, log2L);
-    TQ *qA = Q + rowA * Nu;
-    TQ *qB = Q + rowB * Nu;
-    for (int u = threadIdx.x; u < Nu; u += blockDim.x) {
-        const float2 v = y[u];
-        qA[u] = to_q<TQ>(v.x);
-        if (hasB) qB[u] = to_q<TQ>(-v.y);
+    fft_forward(buf, tw, L, lt, nt);
+    for (int u = lt; u < Nu; u += nt) {
+        const float2 v = buf[pad(u)];
+        if (hasA) Q[rowA * Nu + u] = to_q<TQ>(v.x);
+        if (hasB) Q[rowB * Nu + u] = to_q<TQ>(-v.y);
     }
 }
 
 template <typename TQ>
 cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st) {
     const long long nrows = (long long)p.g.P * p.g.Nv;
-    const long long blocks = (nrows + 1) / 2;
-    const size_t smem = 2 * sizeof(float2) * (size_t)p.L;
+    const long long pairs = (nrows + 1) / 2;
+    const int G = std::max(1, 2048 / p.L);  // 128 threads per CTA up to L = 2048
+    const long long blocks = (pairs + G - 1) / G;
+    const size_t smem = sizeof(float2) * (size_t)G * (p.L + p.L / 16);
     cudaError_t e = cudaFuncSetAttribute(filter_kernel<TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int threads = std::max(32, std::min(kThreads, p.L / 4));
-    filter_kernel<TQ><<<(unsigned)blocks, threads, smem, st>>>(proj, Q, p.H, p.tw, p.L, p.log2L, p.g.Nu,
-                                                               p.g.Nv, nrows, (float)p.g.R);
+    filter_kernel<TQ><<<(unsigned)blocks, G * (p.L / 16), smem, st>>>(proj, Q, p.H, p.tw, p.L, G, p.g.Nu, p.g.Nv,
+                                                                      nrows, (float)p.g.R);
     return cudaGetLastError();
 }
 
