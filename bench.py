@@ -257,12 +257,7 @@ def main():
               for i, name in enumerate(["bounds", "filter", "decompose", "backproject"])}
     assert plan.device_status() == 0, "staging window overflow"
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_1708_07515_gb300.shard import max_over_ranks
 
     ms_total = max_over_ranks(ms_local)
     ms_step = ms_total / args.steps
