@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD_KEY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
+                    help="storage type of the filtered projections (arithmetic stays float32)")
     return ap.parse_args()
 
 
@@ -211,11 +213,11 @@ def main():
     if w.noise:
         phantom.add_noise(proj, w.noise, w.seed + rank)
 
-    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D)
+    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype)
     info = plan.info
     stream = torch.cuda.current_stream()
     proj_d = torch.from_numpy(proj).cuda()
-    Q = torch.empty((w.P, w.Nv, w.Nu), dtype=torch.float32, device="cuda")
+    Q = torch.empty((w.P, w.Nv, w.Nu), dtype=plan.q_torch_dtype, device="cuda")
     S = torch.empty((info["n_squares"], info["Pd"], w.Nv, info["T_stride"]), dtype=torch.float32, device="cuda")
     vol = torch.empty((w.N, w.N, w.N), dtype=torch.float32, device="cuda")
     upd_eff = float(w.N) ** 3 * w.P
@@ -375,7 +377,7 @@ def main():
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: seeded random-ellipsoid phantom, exact cone-beam projections, 1% Gaussian noise",
             "config": {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s,
-                       "D": w.D, "step": "bounds + filter + decompose + backproject",
+                       "D": w.D, "q_storage": args.qtype, "step": "bounds + filter + decompose + backproject",
                        "l2": f"inputs larger than L2 (projections {proj.nbytes / 1e6:.0f} MB, decomposed data "
                              f"{info['decomposed_elems'] * 4 / 1e9:.2f} GB)",
                        "parallelism": f"{world} independent scans, one per GPU"},

@@ -113,14 +113,14 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     ss.Wd = (int)ceil(ext_t) + 5;
     ss.Wd += ss.Wd & 1;  // even width: odd shared-memory row stride
     ss.Rw = (int)ceil(ext_v) + 5;
-    // TMA copies start on a 4-float boundary: up to 3 more columns
-    const int need = (int)ceil(ext_t) + 8;
-    ss.WdT = 0;
-    for (int w : {32, 48, 64, 96, 128})
-        if (need <= w) {
-            ss.WdT = w;
-            break;
-        }
+    // TMA copies start on a 16-byte boundary: up to 3 more float32 columns,
+    // or 7 more 16-bit columns
+    const int need = (int)ceil(ext_t) + 8, need16 = (int)ceil(ext_t) + 12;
+    ss.WdT = ss.WdT16 = 0;
+    for (int w : {128, 96, 64, 48, 32}) {
+        if (need <= w) ss.WdT = w;
+        if (need16 <= w) ss.WdT16 = w;
+    }
 }
 
 }  // namespace fdkod

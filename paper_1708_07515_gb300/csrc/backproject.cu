@@ -225,9 +225,9 @@ cudaError_t launch_t(BpParams prm, int nsq, cudaStream_t st) {
 // two stages of kViewsPerStage views are in flight (copy of stage c+1
 // overlaps the gather of stage c), the per-view set-up is FP32 only, and the
 // inner loop is
-//   v = fma(1/U, i, v0);  m = v + 1.5*2^23 rounded down (= floor(v) in the
-//   low mantissa bits);  fv = v - (m - 1.5*2^23);  four shared loads at
-//   compile-time offsets;  two column lerps pre-weighted by U^-2;  row lerp.
+//   v = fma(1/U, i, v0);  fl = floor(v);  fv = v - fl;  one multiply-add for
+//   the row address;  four shared loads at compile-time offsets;  two column
+//   lerps pre-weighted by U^-2;  row lerp (about 18.7 instructions/update).
 // Waits on the copies are bounded (FDKOD_ERR_TIMEOUT, then drain and exit).
 
 struct BpTmaParams {
@@ -242,25 +242,49 @@ struct BpTmaParams {
     float scale;
 };
 
-// shared-memory load at a compile-time byte offset from a 32-bit address
+// shared-memory load of one window element at a compile-time byte offset
+// from a 32-bit address, widened to float32
+template <typename TS, int OFF>
+struct Lds;
 template <int OFF>
-__device__ __forceinline__ float lds(uint32_t addr) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF) : "memory");
-    return v;
-}
+struct Lds<float, OFF> {
+    static __device__ __forceinline__ float f(uint32_t addr) {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF) : "memory");
+        return v;
+    }
+};
+template <int OFF>
+struct Lds<__nv_bfloat16, OFF> {
+    static __device__ __forceinline__ float f(uint32_t addr) {
+        uint32_t u;
+        asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(u) : "r"(addr), "n"(OFF) : "memory");
+        return __uint_as_float(u << 16);  // bfloat16 is the top half of a float32
+    }
+};
+template <int OFF>
+struct Lds<__half, OFF> {
+    static __device__ __forceinline__ float f(uint32_t addr) {
+        unsigned short h;
+        asm volatile("ld.shared.u16 %0, [%1+%2];" : "=h"(h) : "r"(addr), "n"(OFF) : "memory");
+        return __half2float(__ushort_as_half(h));
+    }
+};
 
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: integers sit in the low mantissa bits
+// address bias: (row + kMagicBits) * 4 WD wraps to row * 4 WD in 32 bits once
+// tbase absorbs -kMagicBits * 4 WD (keeps the unsigned arithmetic explicit)
 constexpr int kMagicBits = 0x4B400000;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-template <bool DIRECT, int WD>
+template <typename TS, bool DIRECT, int WD>
 __global__ void __launch_bounds__(kThreads)
 bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
+    constexpr int ES = (int)sizeof(TS);      // window element size (bytes)
+    constexpr int kAl = 16 / ES;             // copy start alignment (elements)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned staging area (offset from the shared array itself so
     // the compiler keeps shared-memory addressing)
-    float *sm = (float *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    TS *sm = (TS *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
     const uint32_t sbase = tma::smem_u32(sm);
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ float4 s_pa[2][kViewsPerStage];  // cos, sin, 1/d_c, alpha
@@ -334,7 +358,7 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
                 // sample of slack each side for FP32 rounding
                 const int clo = cbase + (int)floorf(tmin) - 1;
                 const int chi = cbase + (int)floorf(tmax) + 2;
-                const int xs = clo & ~3;  // 16-byte aligned start of the copy
+                const int xs = clo & ~(kAl - 1);  // 16-byte aligned start of the copy
                 const int vlo = (int)floorf(vmin) - 1;
                 const int vhi = (int)floorf(vmax) + 2;
                 const int skip = (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1);
@@ -353,7 +377,7 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     auto issue = [&](int c, int st) {
         const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
         tma::fence_proxy_async();
-        tma::mbar_arrive_expect_tx(&bars[st], (uint32_t)(nj * a.RW * WD * (int)sizeof(float)));
+        tma::mbar_arrive_expect_tx(&bars[st], (uint32_t)(nj * a.RW * WD * ES));
         for (int w = 0; w < nj; ++w)
             tma::load_3d(sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride, &tmap, &bars[st], s_tx[st][w],
                          s_ty[st][w], s_tz[st][w]);
@@ -400,19 +424,19 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
                 const float a1 = wgt * (t - tf);
                 const float a0 = wgt - a1;
                 const float vb0 = fmaf(invU, -0.5f * (float)(kZT - 1) - s_zcr[st][w] * dd, pb.w);
-                // 32-bit shared address of sample (row 0, column floor(t)),
-                // pre-offset so that the magic-number bits index the row
-                const uint32_t tbase = sbase + 4u * ((uint32_t)(st * kViewsPerStage + w) * (uint32_t)a.tile_stride +
-                                                     (uint32_t)(int)tf) -
-                                       (uint32_t)kMagicBits * (uint32_t)(4 * WD);
+                // 32-bit shared address of sample (row 0, column floor(t));
+                // the row offset folds into one multiply-add per slice
+                const uint32_t tbase = sbase + (uint32_t)ES * ((uint32_t)(st * kViewsPerStage + w) *
+                                                                    (uint32_t)a.tile_stride + (uint32_t)(int)tf) -
+                                       (uint32_t)kMagicBits * (uint32_t)(ES * WD);
 #pragma unroll
                 for (int i = 0; i < kZT; ++i) {
                     const float v = fmaf(invU, (float)i, vb0);
-                    const float mg = __fadd_rd(v, kMagic);
-                    const float fv = v - (mg - kMagic);
-                    const uint32_t ad = (uint32_t)__float_as_int(mg) * (uint32_t)(4 * WD) + tbase;
-                    const float c0 = fmaf(a1, lds<4>(ad), a0 * lds<0>(ad));
-                    const float c1 = fmaf(a1, lds<4 * WD + 4>(ad), a0 * lds<4 * WD>(ad));
+                    const float fl = floorf(v);
+                    const float fv = v - fl;
+                    const uint32_t ad = (uint32_t)((int)fl + kMagicBits) * (uint32_t)(ES * WD) + tbase;
+                    const float c0 = fmaf(a1, Lds<TS, ES>::f(ad), a0 * Lds<TS, 0>::f(ad));
+                    const float c1 = fmaf(a1, Lds<TS, ES * WD + ES>::f(ad), a0 * Lds<TS, ES * WD>::f(ad));
                     acc[i] = fmaf(fv, c1 - c0, acc[i] + c0);
                 }
             }
@@ -426,43 +450,46 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     }
 }
 
-template <bool DIRECT, int WD>
+template <typename TS, bool DIRECT, int WD>
 cudaError_t launch_tma_t(const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)2 * kViewsPerStage * prm.tile_stride + 128;
-    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<DIRECT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = sizeof(TS) * (size_t)2 * kViewsPerStage * prm.tile_stride + 128;
+    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<TS, DIRECT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.N + kZT - 1) / kZT));
-    bp_tma_kernel<DIRECT, WD><<<grid, kThreads, smem, st>>>(map, prm);
+    bp_tma_kernel<TS, DIRECT, WD><<<grid, kThreads, smem, st>>>(map, prm);
     return cudaGetLastError();
 }
 
-template <bool DIRECT>
+template <typename TS, bool DIRECT>
 cudaError_t launch_tma_w(int WD, const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
     switch (WD) {
-        case 32: return launch_tma_t<DIRECT, 32>(map, prm, nsq, st);
-        case 48: return launch_tma_t<DIRECT, 48>(map, prm, nsq, st);
-        case 64: return launch_tma_t<DIRECT, 64>(map, prm, nsq, st);
-        case 96: return launch_tma_t<DIRECT, 96>(map, prm, nsq, st);
-        case 128: return launch_tma_t<DIRECT, 128>(map, prm, nsq, st);
+        case 32: return launch_tma_t<TS, DIRECT, 32>(map, prm, nsq, st);
+        case 48: return launch_tma_t<TS, DIRECT, 48>(map, prm, nsq, st);
+        case 64: return launch_tma_t<TS, DIRECT, 64>(map, prm, nsq, st);
+        case 96: return launch_tma_t<TS, DIRECT, 96>(map, prm, nsq, st);
+        case 128: return launch_tma_t<TS, DIRECT, 128>(map, prm, nsq, st);
     }
     return cudaErrorInvalidValue;
 }
 
-// The TMA path applies when the source is float32, 16-byte aligned, its
-// rows are whole 16-byte units, and the window fits a box (<= 256 rows).
+// The TMA path applies when the source is 16-byte aligned, its rows are whole
+// 16-byte units, and the window fits a box (<= 256 rows, width an
+// instantiated WD).  The decomposed data is float32; Q may be 16-bit.
 cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
                            cudaStream_t st, bool &launched) {
     launched = false;
-    if (ss.WdT == 0 || ss.Rw > 256 || ((uintptr_t)src & 15) != 0) return cudaSuccess;
-    if (direct && (p.qtype != FDKOD_F32 || (p.g.Nu % 4) != 0)) return cudaSuccess;
+    const int es = (direct && p.qtype != FDKOD_F32) ? 2 : 4;
+    const int WD = es == 4 ? ss.WdT : ss.WdT16;
+    if (WD == 0 || ss.Rw > 256 || ((uintptr_t)src & 15) != 0) return cudaSuccess;
+    if (direct && ((size_t)p.g.Nu * es) % 16 != 0) return cudaSuccess;
     CUtensorMap map;
     uint64_t dims[3], strides[2];
     if (direct) {
         dims[0] = (uint64_t)p.g.Nu;
         dims[1] = (uint64_t)p.g.Nv;
         dims[2] = (uint64_t)p.g.P;
-        strides[0] = (uint64_t)p.g.Nu * sizeof(float);
+        strides[0] = (uint64_t)p.g.Nu * es;
     } else {
         dims[0] = (uint64_t)p.Tstride;
         dims[1] = (uint64_t)p.g.Nv;
@@ -470,8 +497,11 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
         strides[0] = (uint64_t)p.Tstride * sizeof(float);
     }
     strides[1] = strides[0] * dims[1];
-    const uint32_t box[3] = {(uint32_t)ss.WdT, (uint32_t)ss.Rw, 1u};
-    cudaError_t e = encode_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src, dims, strides, box);
+    const uint32_t box[3] = {(uint32_t)WD, (uint32_t)ss.Rw, 1u};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (p.qtype == FDKOD_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    cudaError_t e = encode_map_3d(&map, dt, src, dims, strides, box);
     if (e != cudaSuccess) return cudaSuccess;  // not encodable: generic path
     BpTmaParams a{};
     a.vol = vol;
@@ -486,7 +516,8 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
     a.tps = ss.tiles_per_side;
     a.Pd = p.Pd;
     a.RW = ss.Rw;
-    a.tile_stride = (ss.Rw * ss.WdT + 31) & ~31;
+    // elements per staged window, a 128-byte multiple
+    a.tile_stride = (ss.Rw * WD + (128 / es - 1)) & ~(128 / es - 1);
     if (direct) {
         a.nviews = p.g.P;
         a.vstep = 1;
@@ -497,7 +528,13 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
         a.scale = (float)(M_PI / (double)p.Pd);
     }
     launched = true;
-    return direct ? launch_tma_w<true>(ss.WdT, map, a, ss.nsq, st) : launch_tma_w<false>(ss.WdT, map, a, ss.nsq, st);
+    if (!direct) return launch_tma_w<float, false>(WD, map, a, ss.nsq, st);
+    switch (p.qtype) {
+        case FDKOD_F32: return launch_tma_w<float, true>(WD, map, a, ss.nsq, st);
+        case FDKOD_BF16: return launch_tma_w<__nv_bfloat16, true>(WD, map, a, ss.nsq, st);
+        case FDKOD_F16: return launch_tma_w<__half, true>(WD, map, a, ss.nsq, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace

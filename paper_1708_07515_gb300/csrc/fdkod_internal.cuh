@@ -36,7 +36,7 @@ struct SquareSet {
     // FP64 sweep over every tile and view; WdT is the width of the TMA path
     // (4-element alignment slack, rounded up to a kernel instantiation, 0
     // when no instantiation is wide enough)
-    int Wd = 0, Rw = 0, WdT = 0;
+    int Wd = 0, Rw = 0, WdT = 0, WdT16 = 0;  // WdT16: the same for 16-bit windows
     int tiles_per_side = 1;  // 16-voxel tiles per square side
 };
 

@@ -180,3 +180,59 @@ def test_full_size_512_sampled_slices(fd, oracle_mod):
     _cmp(od, oracle_mod.fdkod_slices(Q, R, w.N, w.s, w.D, zs), "FDK-OD 512")
     _cmp(pl, oracle_mod.fdk_slices(Q, R, w.N, zs), "plain FDK 512")
     plan.close()
+
+
+# ---- precision forms: Q stored as bfloat16 / float16 (FP32 arithmetic) ----
+
+_TORCH16 = {"bf16": "bfloat16", "f16": "float16"}
+
+
+def _round16(Q, qtype):
+    t = torch.from_numpy(Q.astype(np.float32)).to(getattr(torch, _TORCH16[qtype]))
+    return t, t.float().numpy()
+
+
+@pytest.mark.parametrize("qtype", ["bf16", "f16"])
+@pytest.mark.parametrize("N,P,s,D,Nu,Nv", [(64, 96, 3, 4, 64, 64), (50, 60, 2, 3, 53, 47)])
+def test_precision_forms_parity_on_identical_inputs(fd, oracle_mod, qtype, N, P, s, D, Nu, Nv):
+    """Both sides read the same 16-bit-rounded Q; the arithmetic is FP32 on
+    the GPU and FP64 in the oracle, so the FP32 bar applies."""
+    _, Q, R = _q_from_phantom(oracle_mod, N, P, 10, 600 + N + D, Nu=Nu, Nv=Nv)
+    Q16, Qr = _round16(Q, qtype)
+    plan = fd.Plan(R, N, Nu, Nv, P, s, D, qtype=qtype)
+    Qd = Q16.cuda()
+    _cmp(plan.backproject(Qd).cpu().numpy(), oracle_mod.fdkod(Qr, R, N, s, D), f"FDK-OD {qtype}")
+    _cmp(plan.backproject_plain(Qd).cpu().numpy(), oracle_mod.fdk(Qr, R, N), f"plain FDK {qtype}")
+    assert plan.device_status() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("qtype", ["bf16", "f16"])
+def test_filter_writes_16bit_within_rounding(fd, oracle_mod, qtype):
+    N, P = 64, 16
+    R = 4.0 * N
+    p = phantom.project(phantom.make_phantom(700, N, 8), R, N, N, P)
+    plan = fd.Plan(R, N, N, N, P, 0, 1, qtype=qtype)
+    Qg = plan.filter(torch.from_numpy(p).cuda()).float().cpu().numpy().astype(np.float64)
+    Qo = oracle_mod.filter(p, R)
+    # round-to-nearest storage: half an ulp, 2^-9 (bf16) or 2^-12 (f16)
+    # relative, plus the f16 subnormal spacing and the FFT round-off
+    rel = 2.0 ** -8 if qtype == "bf16" else 2.0 ** -11
+    fft = 2 * np.log2(plan.info["fft_length"]) * 2.0 ** -24 * 2 * np.abs(Qo).max() * np.sqrt(N)
+    assert np.all(np.abs(Qg - Qo) <= rel * np.abs(Qo) + 2.0 ** -24 + fft)
+    plan.close()
+
+
+@pytest.mark.parametrize("qtype,bound", [("bf16", 5e-3), ("f16", 1e-3)])
+def test_precision_form_error_against_fp64(fd, oracle_mod, qtype, bound):
+    """The storage rounding's own cost: 16-bit Q against the FP64 oracle on
+    unrounded Q (the bench states the measured value per workload)."""
+    N, P, s, D = 64, 96, 3, 4
+    _, Q, R = _q_from_phantom(oracle_mod, N, P, 10, 800)
+    Q16, _ = _round16(Q, qtype)
+    plan = fd.Plan(R, N, N, N, P, s, D, qtype=qtype)
+    got = plan.backproject(Q16.cuda()).cpu().numpy().astype(np.float64)
+    want = oracle_mod.fdkod(Q, R, N, s, D)
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < bound, rel
+    plan.close()
