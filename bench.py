@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD_KEY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--batched", action="store_true",
+                    help="64 volumes of uneven size (N in {64..384}, P = 1.4 N) in one CUDA graph")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the filtered projections (arithmetic stays float32)")
     return ap.parse_args()
@@ -180,6 +183,26 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def recorded_bp_traffic(workload: str):
+    """DRAM bytes per backprojection launch from the committed ncu summary,
+    or None when the summary is for another workload or the kernel's source
+    text has changed since the counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", "dram_traffic_fdkod_512.md")).read()
+        src = open(os.path.join(ROOT, "paper_1708_07515_gb300", "csrc", "backproject.cu")).read()
+        a = src.index("template <typename TS, bool DIRECT, int WD>\n__global__")
+        b = src.index("template <typename TS, bool DIRECT, int WD>\ncudaError_t launch_tma_t")
+        fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith("bp_traffic_"))
+        if fields.get("bp_traffic_workload") != workload:
+            return None
+        if fields.get("bp_traffic_kernel_sha256") != hashlib.sha256(src[a:b].encode()).hexdigest():
+            return None
+        return int(fields["bp_traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -187,10 +210,53 @@ def measured_peaks():
         return {}
 
 
+def batched_main(args):
+    """The batched form: 64 seeded volumes of uneven size, (s, D) per volume
+    from the autotuner, all stages of all volumes in one CUDA graph."""
+    import torch
+
+    import phantom
+    from paper_1708_07515_gb300 import autotune
+    from paper_1708_07515_gb300.batch import BatchReconstructor, Instance
+    torch.cuda.set_device(0)
+    work = phantom.batched_workload()
+    insts = [Instance(R, N, N, N, P) for N, P, R, _ in work]
+    projs = [phantom.project_gpu(phantom.make_phantom(sd, N, 20), R, N, N, P) for N, P, R, sd in work]
+    rates = autotune.measure_rates()
+    br = BatchReconstructor(insts, rates=rates)
+    br.load(projs)
+    br.capture()
+    for _ in range(args.warmup):
+        br.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        a.record(br.stream)
+        for _ in range(args.steps):
+            with torch.cuda.stream(br.stream):
+                br.graph.replay()
+        b.record(br.stream)
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    upd = sum(float(i.N) ** 3 * i.P for i in insts)
+    out = {"metric": METRIC, "value": upd / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (projections generated on the GPU)",
+           "config": {"workload": "batched_64_volumes_N64-384_P1.4N", "volumes": len(insts),
+                      "step": "one CUDA-graph launch: bounds + filter + decompose + backproject of every volume",
+                      "choices": [[i.N, i.P, i.s, i.D] for i in insts], "rates": list(rates)},
+           "gpu_launches": 4 * len(insts) * args.steps, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    br.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.batched:
+        return batched_main(args)
     import torch
     import torch.distributed as dist
 
@@ -209,9 +275,20 @@ def main():
     w = phantom.WORKLOADS[args.workload]
     # each rank reconstructs its own scan (independent problems, weak scaling)
     ell = phantom.make_phantom(w.seed + rank, w.N, w.n_ell)
-    proj = phantom.project(ell, w.R, w.Nu, w.Nv, w.P)
-    if w.noise:
-        phantom.add_noise(proj, w.noise, w.seed + rank)
+    gpu_inputs = w.N > 512  # the CPU generator would take minutes
+    if gpu_inputs:
+        proj_t = phantom.project_gpu(ell, w.R, w.Nu, w.Nv, w.P)
+        if w.noise:
+            gen = torch.Generator(device="cuda").manual_seed(w.seed + rank + 7919)
+            sigma = w.noise * float(proj_t.max())
+            for k in range(w.P):
+                proj_t[k].add_(torch.randn(proj_t[k].shape, generator=gen, device="cuda"), alpha=sigma)
+        proj = proj_t.cpu().numpy()
+        del proj_t
+    else:
+        proj = phantom.project(ell, w.R, w.Nu, w.Nv, w.P)
+        if w.noise:
+            phantom.add_noise(proj, w.noise, w.seed + rank)
 
     plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype)
     info = plan.info
@@ -289,10 +366,11 @@ def main():
     # back; uploads and read-backs run on their own streams, double-buffered,
     # so they overlap the neighbouring steps' compute (the plan's workspace is
     # used by one step at a time on the compute stream)
-    proj_h = torch.from_numpy(proj).pin_memory()
-    vol_h = [torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory() for _ in range(2)]
-    proj_dd = [proj_d, torch.empty_like(proj_d)]
-    vol_dd = [vol, torch.empty_like(vol)]
+    if not args.no_e2e:
+        proj_h = torch.from_numpy(proj).pin_memory()
+        vol_h = [torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory() for _ in range(2)]
+        proj_dd = [proj_d, torch.empty_like(proj_d)]
+        vol_dd = [vol, torch.empty_like(vol)]
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
     cst = int(stream.cuda_stream)
 
@@ -324,11 +402,14 @@ def main():
         torch.cuda.synchronize()
         return t_start.elapsed_time(t_end)
 
-    e2e_run(max(2, min(args.warmup, 3)))
-    n_e2e = max(2, min(args.steps, 10))
-    barrier()
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e2e_run(n_e2e)) / n_e2e
+    if args.no_e2e:
+        ms_e2e, n_e2e = None, 0
+    else:
+        e2e_run(max(2, min(args.warmup, 3)))
+        n_e2e = max(2, min(args.steps, 10))
+        barrier()
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e2e_run(n_e2e)) / n_e2e
 
     # --- accuracy at the measured configuration, against the FP64 oracle
     extra = {}
@@ -375,20 +456,25 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic: seeded random-ellipsoid phantom, exact cone-beam projections, 1% Gaussian noise",
+            "data": ("synthetic: seeded random-ellipsoid phantom, exact cone-beam projections"
+                     + (f", {100 * w.noise:g}% Gaussian noise" if w.noise else "")
+                     + (" (projections generated on the GPU)" if gpu_inputs else "")),
             "config": {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s,
                        "D": w.D, "q_storage": args.qtype, "step": "bounds + filter + decompose + backproject",
                        "l2": f"inputs larger than L2 (projections {proj.nbytes / 1e6:.0f} MB, decomposed data "
                              f"{info['decomposed_elems'] * 4 / 1e9:.2f} GB)",
                        "parallelism": f"{world} independent scans, one per GPU"},
-            "e2e": {"value": world * upd_eff / (ms_e2e * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": proj_h.numel() * 4, "d2h_bytes_per_step": vol_h[0].numel() * 4,
-                    "ms_per_step": ms_e2e, "steps": n_e2e,
-                    "note": "uploads and read-backs on their own streams, overlapping neighbouring steps"},
+            "e2e": None if ms_e2e is None else {
+                "value": world * upd_eff / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": proj.nbytes, "d2h_bytes_per_step": w.N ** 3 * 4,
+                "ms_per_step": ms_e2e, "steps": n_e2e,
+                "note": "uploads and read-backs on their own streams, overlapping neighbouring steps"},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "alu", "kernel": "bp_kernel (FDK-OD backprojection)",
+            "roofline": {"bound": "alu", "kernel": "bp_tma_kernel (FDK-OD backprojection)",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops, "traffic": None,
+                         "frac": achieved_tflops / peak_tflops,
+                         "traffic": recorded_bp_traffic(args.workload if args.qtype == "f32" else ""),
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "peak_note": f"152 SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
                          "per_launch_updates": upd_bp, "flop_per_update": FLOP_PER_UPDATE,
                          "avg_launch_ms": bp_ms},

@@ -97,6 +97,18 @@ typedef struct {
  */
 int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out);
 
+/* Flags of fdkod_plan_ex. */
+#define FDKOD_PLAN_NO_WORKSPACE 1 /* do not allocate the whole-volume decomposed-data workspace */
+
+/*
+ * fdkod_plan with flags.  FDKOD_PLAN_NO_WORKSPACE leaves out the
+ * 4^s * (P/D) * Nv * T_stride float workspace of fdkod_backproject: such a
+ * plan serves the slab-wise entry points below (piecemeal reconstruction,
+ * Sec. 2.2), and fdkod_backproject then returns FDKOD_ERR_INVALID_ARG when
+ * D > 1.  Other flags: INVALID_ARG.  Otherwise as fdkod_plan.
+ */
+int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int flags, fdkod_plan_t **out);
+
 /* Release a plan (NULL is ignored).  Waits for the device to finish. */
 void fdkod_destroy(fdkod_plan_t *plan);
 
@@ -162,6 +174,41 @@ int fdkod_backproject_decomposed(fdkod_plan_t *plan, const float *S, float *vol,
  * results are identical to the plan's.  Errors: INVALID_ARG, CUDA.
  */
 int fdkod_compute_bounds(fdkod_plan_t *plan, uintptr_t stream);
+
+/*
+ * Piecemeal reconstruction (Sec. 2.2: FDK-OD needs only the part of the
+ * sinogram its part of the image uses).  A slab of slices z0 .. z0+nz-1
+ * reads only the detector rows the row formula b = z R / (R + x cos b +
+ * y sin b) can reach; these three calls let a caller hold just those rows,
+ * the slab's decomposed data and the slab's volume on the device.
+ *
+ * fdkod_slab_rows: the band [*v0, *v0 + *nrows) of detector rows slices
+ * z0 .. z0+nz-1 need (host arithmetic, no device work).  Errors:
+ * INVALID_ARG (null, empty or out-of-range slab).
+ */
+int fdkod_slab_rows(const fdkod_plan_t *plan, int z0, int nz, int32_t *v0, int32_t *nrows);
+
+/*
+ * fdkod_filter_rows: the filter of fdkod_filter on detector rows
+ * v0 .. v0+nrows-1 only.  proj_rows, Q_rows: device [P][nrows][Nu] (float32,
+ * plan's qtype).  Errors: INVALID_ARG (also for a band outside the
+ * detector), CUDA.
+ */
+int fdkod_filter_rows(fdkod_plan_t *plan, const float *proj_rows, int v0, int nrows, void *Q_rows,
+                      uintptr_t stream);
+
+/*
+ * fdkod_backproject_slab: fdkod_backproject restricted to slices
+ * z0 .. z0+nz-1, reading filtered rows v0 .. v0+nrows-1 only.  Q_rows:
+ * device [P][nrows][Nu] of the plan's qtype; S_work: device float
+ * workspace of n_squares * Pd * nrows * T_stride elements (fdkod_get_info;
+ * unused, may be NULL, when D == 1); vol_slab: device [nz][N][N] float32,
+ * fully overwritten.  The band must contain the rows fdkod_slab_rows
+ * returns for the slab.  Errors: INVALID_ARG (null pointers, slab or band
+ * out of range, band missing needed rows, no S_work with D > 1), CUDA.
+ */
+int fdkod_backproject_slab(fdkod_plan_t *plan, const void *Q_rows, int v0, int nrows, float *S_work, int z0,
+                           int nz, float *vol_slab, uintptr_t stream);
 
 /*
  * Copy the plan's crop bounds to host arrays (each may be NULL):

@@ -22,4 +22,5 @@ from .fdkod import (  # noqa: F401
     fdkod_plan,
     lib_path,
     load,
+    reconstruct_slabs,
 )

@@ -213,7 +213,7 @@ int build_plan(PlanImpl &p, cudaStream_t st) {
     rc = make_fft_tables(p, st);
     if (rc) return rc;
     p.Tstride = (p.od.Tmax + 3) & ~3;
-    if (p.D > 1) {
+    if (p.D > 1 && !p.no_workspace) {
         p.sp_elems = (int64_t)p.od.nsq * p.Pd * p.g.Nv * p.Tstride;
         FDKOD_TRY(dalloc(p, &p.Sp, (size_t)p.sp_elems));
     }
@@ -260,8 +260,13 @@ cudaError_t encode_map_3d(CUtensorMap *map, CUtensorMapDataType dt, const void *
 extern "C" {
 
 int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out) {
+    return fdkod_plan_ex(g, s, D, qtype, 0, out);
+}
+
+int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int flags, fdkod_plan_t **out) {
     if (!g || !out) return FDKOD_ERR_INVALID_ARG;
     *out = nullptr;
+    if (flags & ~FDKOD_PLAN_NO_WORKSPACE) return FDKOD_ERR_INVALID_ARG;
     if (!(g->R > 0.0) || g->N <= 0 || g->Nu <= 0 || g->Nv <= 0 || g->P <= 0 || D <= 0 || !valid_dtype(qtype))
         return FDKOD_ERR_INVALID_ARG;
     const int lim = 1 << 15;
@@ -280,6 +285,7 @@ int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_p
     p.D = D;
     p.Pd = g->P / D;
     p.qtype = qtype;
+    p.no_workspace = (flags & FDKOD_PLAN_NO_WORKSPACE) != 0;
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         delete pl;
@@ -326,6 +332,7 @@ int fdkod_filter(fdkod_plan_t *plan, const float *proj, void *Q, uintptr_t strea
 int fdkod_backproject(fdkod_plan_t *plan, const void *Q, float *vol, uintptr_t stream) {
     if (!plan || !Q || !vol) return FDKOD_ERR_INVALID_ARG;
     PlanImpl &p = plan->impl;
+    if (p.D > 1 && !p.Sp) return FDKOD_ERR_INVALID_ARG;  // plan made without a workspace
     cudaStream_t st = (cudaStream_t)stream;
     if (p.D == 1) return cuda_status(launch_backproject(p, p.od, true, Q, vol, st));
     FDKOD_TRY(launch_decompose(p, Q, p.Sp, st));
@@ -377,6 +384,64 @@ int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream) {
     if (h & 2) return FDKOD_ERR_TIMEOUT;
     if (h & 1) return FDKOD_ERR_BOUNDS;
     return FDKOD_OK;
+}
+
+int fdkod_slab_rows(const fdkod_plan_t *plan, int z0, int nz, int32_t *v0, int32_t *nrows) {
+    if (!plan || !v0 || !nrows) return FDKOD_ERR_INVALID_ARG;
+    const fdkod_geometry &g = plan->impl.g;
+    if (z0 < 0 || nz < 1 || z0 + nz > g.N) return FDKOD_ERR_INVALID_ARG;
+    // U = (R + x cos b + y sin b) / R lies in [1 - r/R, 1 + r/R] for the
+    // largest in-slice radius r; the row is z / U + (Nv-1)/2 (Sec. 2.2)
+    const double rmax = M_SQRT2 * 0.5 * (double)(g.N - 1);
+    const double vc = 0.5 * (double)(g.Nv - 1);
+    double lo = INFINITY, hi = -INFINITY;
+    const int zs[2] = {z0, z0 + nz - 1};
+    for (int i = 0; i < 2; ++i) {
+        const double z = (double)zs[i] - 0.5 * (double)(g.N - 1);
+        for (double U : {1.0 - rmax / g.R, 1.0 + rmax / g.R}) {
+            const double v = z / U + vc;
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+    }
+    const int a = std::max(0, (int)floor(lo));
+    const int b = std::min(g.Nv, (int)floor(hi) + 2);
+    *v0 = a;
+    *nrows = std::max(1, b - a);
+    if (a >= g.Nv) *v0 = g.Nv - 1;
+    return FDKOD_OK;
+}
+
+int fdkod_filter_rows(fdkod_plan_t *plan, const float *proj_rows, int v0, int nrows, void *Q_rows,
+                      uintptr_t stream) {
+    if (!plan || !proj_rows || !Q_rows) return FDKOD_ERR_INVALID_ARG;
+    const PlanImpl &p = plan->impl;
+    if (v0 < 0 || nrows < 1 || v0 + nrows > p.g.Nv) return FDKOD_ERR_INVALID_ARG;
+    Band b;
+    b.row0 = v0;
+    b.nrows = nrows;
+    return cuda_status(launch_filter(p, proj_rows, Q_rows, (cudaStream_t)stream, b));
+}
+
+int fdkod_backproject_slab(fdkod_plan_t *plan, const void *Q_rows, int v0, int nrows, float *S_work, int z0, int nz,
+                           float *vol_slab, uintptr_t stream) {
+    if (!plan || !Q_rows || !vol_slab) return FDKOD_ERR_INVALID_ARG;
+    PlanImpl &p = plan->impl;
+    if (v0 < 0 || nrows < 1 || v0 + nrows > p.g.Nv || z0 < 0 || nz < 1 || z0 + nz > p.g.N)
+        return FDKOD_ERR_INVALID_ARG;
+    if (p.D > 1 && !S_work) return FDKOD_ERR_INVALID_ARG;
+    int32_t need0 = 0, needn = 0;
+    fdkod_slab_rows(plan, z0, nz, &need0, &needn);
+    if (need0 < v0 || need0 + needn > v0 + nrows) return FDKOD_ERR_INVALID_ARG;  // band misses rows
+    Band b;
+    b.row0 = v0;
+    b.nrows = nrows;
+    b.zoff = z0;
+    b.nz = nz;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p.D == 1) return cuda_status(launch_backproject(p, p.od, true, Q_rows, vol_slab, st, b));
+    FDKOD_TRY(launch_decompose(p, Q_rows, S_work, st, b));
+    return cuda_status(launch_backproject(p, p.od, false, S_work, vol_slab, st, b));
 }
 
 const char *fdkod_strerror(int status) {

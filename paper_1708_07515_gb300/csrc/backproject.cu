@@ -44,6 +44,8 @@ struct BpParams {
     int *status;
     long long sq_stride, view_stride, row_stride;  // source layout (elements)
     int src_cols, src_rows;
+    int row0;                // detector row held in the source's row 0
+    int zoff, nz;            // slices zoff .. zoff + nz - 1, written to vol[z - zoff]
     int N, P, Nv, m, tps;    // tps: tiles per square side
     int nviews, vstep;       // views summed; table view index = j * vstep
     int Wd, Rw, J;           // staging window and views per chunk
@@ -79,8 +81,8 @@ bp_generic_kernel(BpParams a) {
     const int y0 = iy0 + (tt / a.tps) * kTile;
     if (x0 > ix1 || y0 > iy1) return;  // ragged square: empty tile (uniform per CTA)
     const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
-    const int z0 = blockIdx.y * kZT;
-    const int z1 = min(z0 + kZT - 1, a.N - 1);
+    const int z0 = a.zoff + blockIdx.y * kZT;
+    const int z1 = min(z0 + kZT - 1, a.zoff + a.nz - 1);
 
     const float half_n = 0.5f * (float)(a.N - 1);
     const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;  // square centre (exact half-integers)
@@ -160,7 +162,7 @@ bp_generic_kernel(BpParams a) {
         for (int rid = warp; rid < nj * a.Rw; rid += kWarps) {
             const int w = rid / a.Rw;
             const int r = rid - w * a.Rw;
-            const int v = s_vlo[w] + r;
+            const int v = s_vlo[w] + r - a.row0;  // row of the source
             const bool rok = v >= 0 && v < a.src_rows;
             const TS *row = src + s_off[w] + (long long)v * a.row_stride;
             float *dst = win + (size_t)rid * WS;
@@ -203,17 +205,16 @@ bp_generic_kernel(BpParams a) {
     if (active) {
 #pragma unroll
         for (int i = 0; i < kZT; ++i)
-            if (z0 + i <= z1) a.vol[((size_t)(z0 + i) * a.N + y) * a.N + x] = acc[i] * a.scale;
+            if (z0 + i <= z1) a.vol[((size_t)(z0 + i - a.zoff) * a.N + y) * a.N + x] = acc[i] * a.scale;
     }
 }
 
 template <typename TS, bool DIRECT>
 cudaError_t launch_t(BpParams prm, int nsq, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)prm.J * prm.Rw * (prm.Wd + 1);
-    cudaError_t e = cudaFuncSetAttribute(bp_generic_kernel<TS, DIRECT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem<bp_generic_kernel<TS, DIRECT>>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.N + kZT - 1) / kZT));
+    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.nz + kZT - 1) / kZT));
     bp_generic_kernel<TS, DIRECT><<<grid, kThreads, smem, st>>>(prm);
     return cudaGetLastError();
 }
@@ -238,7 +239,9 @@ struct BpTmaParams {
     int *status;
     int N, P, Nv, m, tps;
     int nviews, vstep, Pd;
-    int RW, tile_stride;  // window rows; floats per staged window (128-byte multiple)
+    int RW, tile_stride;  // window rows; elements per staged window (128-byte multiple)
+    int row0;             // detector row held in the source's row 0
+    int zoff, nz;         // slices zoff .. zoff + nz - 1, written to vol[z - zoff]
     float scale;
 };
 
@@ -304,8 +307,8 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     const int y0 = iy0 + (tt / a.tps) * kTile;
     if (x0 > ix1 || y0 > iy1) return;  // ragged square: empty tile (uniform per CTA)
     const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
-    const int z0 = blockIdx.y * kZT;
-    const int z1 = min(z0 + kZT - 1, a.N - 1);
+    const int z0 = a.zoff + blockIdx.y * kZT;
+    const int z1 = min(z0 + kZT - 1, a.zoff + a.nz - 1);
 
     const float half_n = 0.5f * (float)(a.N - 1);
     const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;
@@ -368,7 +371,7 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
                                              (ph - ((float)vlo - vcd)) + pl);
                 s_zcr[st][warp] = zcr;
                 s_tx[st][warp] = xs;
-                s_ty[st][warp] = vlo;
+                s_ty[st][warp] = vlo - a.row0;  // row of the source (out of range: zero fill)
                 s_tz[st][warp] = DIRECT ? k : q * a.Pd + j;
                 s_skip[st][warp] = skip;
             }
@@ -446,17 +449,16 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     if (active) {
 #pragma unroll
         for (int i = 0; i < kZT; ++i)
-            if (z0 + i <= z1) a.vol[((size_t)(z0 + i) * a.N + y) * a.N + x] = acc[i] * a.scale;
+            if (z0 + i <= z1) a.vol[((size_t)(z0 + i - a.zoff) * a.N + y) * a.N + x] = acc[i] * a.scale;
     }
 }
 
 template <typename TS, bool DIRECT, int WD>
 cudaError_t launch_tma_t(const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
     const size_t smem = sizeof(TS) * (size_t)2 * kViewsPerStage * prm.tile_stride + 128;
-    cudaError_t e = cudaFuncSetAttribute(bp_tma_kernel<TS, DIRECT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = ensure_smem<bp_tma_kernel<TS, DIRECT, WD>>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.N + kZT - 1) / kZT));
+    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.nz + kZT - 1) / kZT));
     bp_tma_kernel<TS, DIRECT, WD><<<grid, kThreads, smem, st>>>(map, prm);
     return cudaGetLastError();
 }
@@ -477,7 +479,7 @@ cudaError_t launch_tma_w(int WD, const CUtensorMap &map, const BpTmaParams &prm,
 // 16-byte units, and the window fits a box (<= 256 rows, width an
 // instantiated WD).  The decomposed data is float32; Q may be 16-bit.
 cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
-                           cudaStream_t st, bool &launched) {
+                           cudaStream_t st, const Band &b, bool &launched) {
     launched = false;
     const int es = (direct && p.qtype != FDKOD_F32) ? 2 : 4;
     const int WD = es == 4 ? ss.WdT : ss.WdT16;
@@ -487,12 +489,12 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
     uint64_t dims[3], strides[2];
     if (direct) {
         dims[0] = (uint64_t)p.g.Nu;
-        dims[1] = (uint64_t)p.g.Nv;
+        dims[1] = (uint64_t)b.nrows;
         dims[2] = (uint64_t)p.g.P;
         strides[0] = (uint64_t)p.g.Nu * es;
     } else {
         dims[0] = (uint64_t)p.Tstride;
-        dims[1] = (uint64_t)p.g.Nv;
+        dims[1] = (uint64_t)b.nrows;
         dims[2] = (uint64_t)ss.nsq * p.Pd;
         strides[0] = (uint64_t)p.Tstride * sizeof(float);
     }
@@ -516,6 +518,9 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
     a.tps = ss.tiles_per_side;
     a.Pd = p.Pd;
     a.RW = ss.Rw;
+    a.row0 = b.row0;
+    a.zoff = b.zoff;
+    a.nz = b.nz;
     // elements per staged window, a 128-byte multiple
     a.tile_stride = (ss.Rw * WD + (128 / es - 1)) & ~(128 / es - 1);
     if (direct) {
@@ -540,9 +545,11 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
 }  // namespace
 
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
-                               cudaStream_t st) {
+                               cudaStream_t st, Band b) {
+    if (b.nrows < 0) b.nrows = p.g.Nv;
+    if (b.nz < 0) b.nz = p.g.N;
     bool launched = false;
-    cudaError_t te = try_launch_tma(p, ss, direct, src, vol, st, launched);
+    cudaError_t te = try_launch_tma(p, ss, direct, src, vol, st, b, launched);
     if (launched || te != cudaSuccess) return te;
     BpParams a{};
     a.src = src;
@@ -561,12 +568,15 @@ cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool dire
     const size_t per_view = sizeof(float) * (size_t)ss.Rw * (ss.Wd + 1);
     a.J = (int)std::min<size_t>(kViewsPerChunk, (200u * 1024u) / per_view);
     if (a.J < 1) return cudaErrorInvalidConfiguration;
+    a.row0 = b.row0;
+    a.zoff = b.zoff;
+    a.nz = b.nz;
     if (direct) {
         a.sq_stride = 0;
-        a.view_stride = (long long)p.g.Nv * p.g.Nu;
+        a.view_stride = (long long)b.nrows * p.g.Nu;
         a.row_stride = p.g.Nu;
         a.src_cols = p.g.Nu;
-        a.src_rows = p.g.Nv;
+        a.src_rows = b.nrows;
         a.nviews = p.g.P;
         a.vstep = 1;
         a.scale = (float)(M_PI / (double)p.g.P);
@@ -577,11 +587,11 @@ cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool dire
         }
         return cudaErrorInvalidValue;
     }
-    a.view_stride = (long long)p.g.Nv * p.Tstride;
+    a.view_stride = (long long)b.nrows * p.Tstride;
     a.sq_stride = (long long)p.Pd * a.view_stride;
     a.row_stride = p.Tstride;
     a.src_cols = p.Tstride;
-    a.src_rows = p.g.Nv;
+    a.src_rows = b.nrows;
     a.nviews = p.Pd;
     a.vstep = p.D;
     a.scale = (float)(M_PI / (double)p.Pd);

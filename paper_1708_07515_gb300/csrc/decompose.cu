@@ -101,8 +101,11 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     int *s_crop = (int *)((unsigned char *)sm + sizeof(TQ) * (size_t)kStages * kG * tile_stride);
     float *s_frac = (float *)(s_crop + P);
     __shared__ __align__(8) uint64_t bars[kStages];
+    // per view of a stage: shift fraction, column offset in the box, and the
+    // triangle-tap weights of its two decimated views (D - r and r, the first
+    // zero for the wrapped block), all prepared by the issuing warp
+    __shared__ float4 s_vw[kStages][kG];
     __shared__ int s_off[kStages][kG];
-    __shared__ float s_f[kStages][kG];
 
     const int q = blockIdx.x;
     const int v0 = blockIdx.y * kVB;
@@ -125,7 +128,8 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             const int c = s_crop[kk];
             xs = c & ~(kAlign - 1);
             s_off[slot][tx] = c - xs;
-            s_f[slot][tx] = s_frac[kk];
+            const int r = kp < 0 ? kp + D : kp % D;
+            s_vw[slot][tx] = make_float4(s_frac[kk], kp < 0 ? 0.f : (float)(D - r), (float)r, 0.f);
         }
         __syncwarp();
         if (tx == 0) {
@@ -180,25 +184,26 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
         for (int w = 0; w < nv; ++w) {
             // stream position -> decimated view j0 (-1 for the wrapped block)
             // and tap r, advanced incrementally (no division)
-            const TQ *row = sm + (size_t)(slot * kG + w) * tile_stride + (size_t)ty * Wc + s_off[slot][w] + tx;
-            const float f = s_f[slot][w];
-            const float wa = j0 >= 0 ? (float)(D - r) : 0.f, wb = (float)r;
+            const float4 vw = s_vw[slot][w];
+            const float f = vw.x, wa = vw.y, wb = vw.z;
+                const TQ *row = sm + (size_t)(slot * kG + w) * tile_stride + (size_t)ty * Wc + s_off[slot][w] + tx;
 #pragma unroll
-            for (int i = 0; i < NT; ++i) {
-                // columns t < T read at most T + 3 < Wc elements into the row
-                if (valid[i]) {
-                    const float a0 = sm_ld(row + 32 * i), a1 = sm_ld(row + 32 * i + 1);
-                    const float smp = fmaf(f, a1 - a0, a0);
-                    cur[i] = fmaf(wa, smp, cur[i]);
-                    nxt[i] = fmaf(wb, smp, nxt[i]);
+                for (int i = 0; i < NT; ++i) {
+                    // columns t < T read at most T + 3 < Wc elements into the row
+                    if (valid[i]) {
+                        const float a0 = sm_ld(row + 32 * i), a1 = sm_ld(row + 32 * i + 1);
+                        const float smp = fmaf(f, a1 - a0, a0);
+                        cur[i] = fmaf(wa, smp, cur[i]);
+                        nxt[i] = fmaf(wb, smp, nxt[i]);
+                    }
                 }
-            }
             if (r == D - 1) {
                 if (j0 >= 0 && vok) {
+                    float *o = out + (size_t)j0 * vstride;
 #pragma unroll
                     for (int i = 0; i < NT; ++i) {
                         const int t = tx + 32 * i;
-                        if (t < Tstride) out[(size_t)j0 * vstride + t] = t < T ? cur[i] * inv : 0.f;
+                        if (t < Tstride) o[t] = t < T ? cur[i] * inv : 0.f;
                     }
                 }
                 // the wrapped block (j0 = -1) only seeds decimated view 0
@@ -218,30 +223,30 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
 }
 
 template <typename TQ, int NT>
-cudaError_t launch_tma_nt(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st) {
+cudaError_t launch_tma_nt(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st,
+                          int nrows) {
     const int tile_stride = (kVB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
     const size_t smem = sizeof(TQ) * (size_t)kStages * kG * tile_stride + 128 + 8 * (size_t)p.g.P;
-    cudaError_t e = cudaFuncSetAttribute(decompose_tma_kernel<TQ, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, NT>>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(p.od.nsq, (p.g.Nv + kVB - 1) / kVB);
+    dim3 grid(p.od.nsq, (nrows + kVB - 1) / kVB);
     decompose_tma_kernel<TQ, NT><<<grid, 256, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T, p.status, p.Tstride,
-                                                          p.g.P, p.D, p.Pd, p.g.Nv, Wc, tile_stride);
+                                                          p.g.P, p.D, p.Pd, nrows, Wc, tile_stride);
     return cudaGetLastError();
 }
 
 // TMA applies when Q's rows are whole 16-byte units, Q is 16-byte aligned and
 // a crop box (T_max + one interpolation neighbour + alignment) fits 256 columns.
 template <typename TQ>
-cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, bool &launched) {
+cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows, bool &launched) {
     launched = false;
     constexpr int kAlign = 16 / (int)sizeof(TQ);
     if ((p.g.Nu % kAlign) != 0 || ((uintptr_t)Q & 15) != 0) return cudaSuccess;
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
     if (Wc > 256 || p.Tstride > 256 || p.g.P > 4096) return cudaSuccess;
     CUtensorMap map;
-    const uint64_t dims[3] = {(uint64_t)p.g.Nu, (uint64_t)p.g.Nv, (uint64_t)p.g.P};
-    const uint64_t strides[2] = {(uint64_t)p.g.Nu * sizeof(TQ), (uint64_t)p.g.Nu * p.g.Nv * sizeof(TQ)};
+    const uint64_t dims[3] = {(uint64_t)p.g.Nu, (uint64_t)nrows, (uint64_t)p.g.P};
+    const uint64_t strides[2] = {(uint64_t)p.g.Nu * sizeof(TQ), (uint64_t)p.g.Nu * nrows * sizeof(TQ)};
     const uint32_t box[3] = {(uint32_t)Wc, (uint32_t)kVB, 1u};
     const CUtensorMapDataType dt = sizeof(TQ) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (std::is_same<TQ, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -249,29 +254,30 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     if (encode_map_3d(&map, dt, Q, dims, strides, box) != cudaSuccess) return cudaSuccess;
     launched = true;
     const int nt = (p.Tstride + 31) / 32;
-    if (nt <= 2) return launch_tma_nt<TQ, 2>(p, map, out, Wc, st);
-    if (nt <= 4) return launch_tma_nt<TQ, 4>(p, map, out, Wc, st);
-    return launch_tma_nt<TQ, 8>(p, map, out, Wc, st);
+    if (nt <= 2) return launch_tma_nt<TQ, 2>(p, map, out, Wc, st, nrows);
+    if (nt <= 4) return launch_tma_nt<TQ, 4>(p, map, out, Wc, st, nrows);
+    return launch_tma_nt<TQ, 8>(p, map, out, Wc, st, nrows);
 }
 
 template <typename TQ>
-cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st) {
+cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows) {
     bool launched = false;
-    cudaError_t te = try_tma(p, Q, out, st, launched);
+    cudaError_t te = try_tma(p, Q, out, st, nrows, launched);
     if (launched || te != cudaSuccess) return te;
-    dim3 grid((p.Tstride + kTX - 1) / kTX, (p.g.Nv + kTY - 1) / kTY, p.od.nsq);
+    dim3 grid((p.Tstride + kTX - 1) / kTX, (nrows + kTY - 1) / kTY, p.od.nsq);
     decompose_kernel<TQ><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.Tstride, p.g.P,
-                                                          p.D, p.Pd, p.g.Nv, p.g.Nu);
+                                                          p.D, p.Pd, nrows, p.g.Nu);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st) {
+cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b) {
+    const int nrows = b.nrows < 0 ? p.g.Nv : b.nrows;
     switch (p.qtype) {
-        case FDKOD_F32: return launch_t(p, (const float *)Q, out, st);
-        case FDKOD_BF16: return launch_t(p, (const __nv_bfloat16 *)Q, out, st);
-        case FDKOD_F16: return launch_t(p, (const __half *)Q, out, st);
+        case FDKOD_F32: return launch_t(p, (const float *)Q, out, st, nrows);
+        case FDKOD_BF16: return launch_t(p, (const __nv_bfloat16 *)Q, out, st, nrows);
+        case FDKOD_F16: return launch_t(p, (const __half *)Q, out, st, nrows);
     }
     return cudaErrorInvalidValue;
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/fdkod.h"
 
 namespace fdkod {
@@ -60,19 +62,50 @@ struct PlanImpl {
     float *Sp = nullptr;
     int Tstride = 0;
     int64_t sp_elems = 0;
+    bool no_workspace = false; // made with FDKOD_PLAN_NO_WORKSPACE
     int *status = nullptr;     // device status word
     int64_t device_bytes = 0;
 };
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than any earlier one on this device (one static record per kernel and
+// device, the kernel being the template argument), so steady-state
+// launches -- and launches recorded into a CUDA graph -- make no attribute
+// call.
+template <auto Kernel>
+cudaError_t ensure_smem(size_t bytes) {
+    constexpr int kDevices = 64;
+    static std::atomic<size_t> set[kDevices];  // one record per kernel and device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices)
+        return cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes <= set[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) {
+        size_t cur = set[dev].load();
+        while (cur < bytes && !set[dev].compare_exchange_weak(cur, bytes)) {
+        }
+    }
+    return e;
+}
+
 // host: backprojection staging windows of a square set (cs = cos/sin per view)
 void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs);
 
+// Part of the volume and detector a launch works on: detector rows
+// row0 .. row0 + nrows - 1 are the rows held by the source arrays (Q, the
+// decomposed data), slices zoff .. zoff + nz - 1 are written to vol[z - zoff].
+// The defaults (nrows, nz < 0) mean the whole detector and volume.
+struct Band {
+    int row0 = 0, nrows = -1, zoff = 0, nz = -1;
+};
+
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_bounds(const PlanImpl &p, SquareSet &ss, cudaStream_t st);
-cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st);
-cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st);
+cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b = Band{});
+cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b = Band{});
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
-                               float *vol, cudaStream_t st);
+                               float *vol, cudaStream_t st, Band b = Band{});
 
 }  // namespace fdkod
 

@@ -176,7 +176,8 @@ __device__ __forceinline__ void fft_forward(float2 *buf, const float2 *tw, int L
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
-              const float2 *__restrict__ tw, int L, int G, int Nu, int Nv, long long nrows, float R) {
+              const float2 *__restrict__ tw, int L, int G, int Nu, int Nv, int row0, int rows_per_view,
+              long long nrows, float R) {
     extern __shared__ float2 z[];
     const int nt = L / 16;
     const int g = threadIdx.x / nt, lt = threadIdx.x % nt;
@@ -184,8 +185,9 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
     const long long rowA = 2LL * ((long long)blockIdx.x * G + g);
     const long long rowB = rowA + 1;
     const bool hasA = rowA < nrows, hasB = rowB < nrows;
-    const float bA = (float)(rowA % Nv) - 0.5f * (float)(Nv - 1);
-    const float bB = (float)(rowB % Nv) - 0.5f * (float)(Nv - 1);
+    // detector row of each input row (the input may hold rows row0 .. of each view)
+    const float bA = (float)(row0 + (int)(rowA % rows_per_view)) - 0.5f * (float)(Nv - 1);
+    const float bB = (float)(row0 + (int)(rowB % rows_per_view)) - 0.5f * (float)(Nv - 1);
     const float R2 = R * R;
     for (int i = lt; i < L; i += nt) {
         float2 v = make_float2(0.f, 0.f);
@@ -215,27 +217,27 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
 }
 
 template <typename TQ>
-cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st) {
-    const long long nrows = (long long)p.g.P * p.g.Nv;
+cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st, int row0, int rows_per_view) {
+    const long long nrows = (long long)p.g.P * rows_per_view;
     const long long pairs = (nrows + 1) / 2;
     const int G = std::max(1, 2048 / p.L);  // 128 threads per CTA up to L = 2048
     const long long blocks = (pairs + G - 1) / G;
     const size_t smem = sizeof(float2) * (size_t)G * (p.L + p.L / 16);
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel<TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = ensure_smem<filter_kernel<TQ>>(smem);
     if (e != cudaSuccess) return e;
     filter_kernel<TQ><<<(unsigned)blocks, G * (p.L / 16), smem, st>>>(proj, Q, p.H, p.tw, p.L, G, p.g.Nu, p.g.Nv,
-                                                                      nrows, (float)p.g.R);
+                                                                      row0, rows_per_view, nrows, (float)p.g.R);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st) {
+cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b) {
+    const int rows = b.nrows < 0 ? p.g.Nv : b.nrows;
     switch (p.qtype) {
-        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st);
-        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st);
-        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st);
+        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st, b.row0, rows);
+        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st, b.row0, rows);
+        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st, b.row0, rows);
     }
     return cudaErrorInvalidValue;
 }

@@ -54,6 +54,10 @@ def load():
             vp, i, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
             sig = {
                 "fdkod_plan": (i, [ctypes.POINTER(Geometry), i, i, i, ctypes.POINTER(vp)]),
+                "fdkod_plan_ex": (i, [ctypes.POINTER(Geometry), i, i, i, i, ctypes.POINTER(vp)]),
+                "fdkod_slab_rows": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+                "fdkod_filter_rows": (i, [vp, vp, i, i, vp, u]),
+                "fdkod_backproject_slab": (i, [vp, vp, i, i, vp, i, i, vp, u]),
                 "fdkod_destroy": (None, [vp]),
                 "fdkod_get_info": (i, [vp, ctypes.POINTER(PlanInfo)]),
                 "fdkod_filter": (i, [vp, vp, vp, u]),
@@ -98,10 +102,15 @@ def _dev_ptr(t, what):
 
 # ---- C-named functions -------------------------------------------------------
 
-def fdkod_plan(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: int = FDKOD_F32) -> int:
+FDKOD_PLAN_NO_WORKSPACE = 1
+
+
+def fdkod_plan(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: int = FDKOD_F32,
+               flags: int = 0) -> int:
     g = Geometry(float(R), int(N), int(Nu), int(Nv), int(P))
     out = ctypes.c_void_p()
-    _check(load().fdkod_plan(ctypes.byref(g), int(s), int(D), int(qtype), ctypes.byref(out)), "fdkod_plan")
+    _check(load().fdkod_plan_ex(ctypes.byref(g), int(s), int(D), int(qtype), int(flags), ctypes.byref(out)),
+           "fdkod_plan")
     return out.value
 
 
@@ -160,10 +169,11 @@ def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
 class Plan:
     """A plan for one geometry, decomposition level s and decimation D."""
 
-    def __init__(self, R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: str = "f32"):
+    def __init__(self, R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: str = "f32",
+                 workspace: bool = True):
         self.R, self.N, self.Nu, self.Nv, self.P, self.s, self.D = float(R), N, Nu, Nv, P, s, D
         self.qtype = qtype
-        self.handle = fdkod_plan(R, N, Nu, Nv, P, s, D, _DTYPES[qtype])
+        self.handle = fdkod_plan(R, N, Nu, Nv, P, s, D, _DTYPES[qtype], 0 if workspace else FDKOD_PLAN_NO_WORKSPACE)
         info = PlanInfo()
         _check(load().fdkod_get_info(self.handle, ctypes.byref(info)), "fdkod_get_info")
         self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
@@ -230,6 +240,34 @@ class Plan:
         import torch
         fdkod_compute_bounds(self.handle, torch.cuda.current_stream().cuda_stream if stream is None else stream)
 
+    # -- piecemeal (slab-wise) reconstruction --
+    def slab_rows(self, z0: int, nz: int) -> tuple[int, int]:
+        v0, n = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fdkod_slab_rows(self.handle, int(z0), int(nz), ctypes.byref(v0), ctypes.byref(n)),
+               "fdkod_slab_rows")
+        return v0.value, n.value
+
+    def filter_rows(self, proj_rows, v0: int, Q=None, stream=None):
+        import torch
+        if Q is None:
+            Q = torch.empty(proj_rows.shape, dtype=self.q_torch_dtype, device=proj_rows.device)
+        _check(load().fdkod_filter_rows(self.handle, _dev_ptr(proj_rows, "proj_rows"), int(v0), int(proj_rows.shape[1]),
+                                        _dev_ptr(Q, "Q_rows"), _stream(proj_rows, stream)), "fdkod_filter_rows")
+        return Q
+
+    def slab_workspace_elems(self, nrows: int) -> int:
+        return 0 if self.D == 1 else self.info["n_squares"] * self.info["Pd"] * int(nrows) * self.info["T_stride"]
+
+    def backproject_slab(self, Q_rows, v0: int, S_work, z0: int, nz: int, vol=None, stream=None):
+        import torch
+        if vol is None:
+            vol = torch.empty((nz, self.N, self.N), dtype=torch.float32, device=Q_rows.device)
+        sw = _dev_ptr(S_work, "S_work") if S_work is not None else ctypes.c_void_p()
+        _check(load().fdkod_backproject_slab(self.handle, _dev_ptr(Q_rows, "Q_rows"), int(v0), int(Q_rows.shape[1]), sw,
+                                             int(z0), int(nz), _dev_ptr(vol, "vol_slab"), _stream(Q_rows, stream)),
+               "fdkod_backproject_slab")
+        return vol
+
     def bounds(self) -> dict:
         return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)
 
@@ -237,3 +275,27 @@ class Plan:
         import torch
         st = int(torch.cuda.current_stream().cuda_stream) if stream is None else int(stream)
         return int(load().fdkod_last_device_status(self.handle, st))
+
+
+def reconstruct_slabs(plan: Plan, proj_host, slab: int, out=None):
+    """Piecemeal FDK-OD (Sec. 2.2): for each slab of `slab` slices, upload only
+    the detector rows it needs, filter them, decompose and backproject the
+    slab, and copy it back.  proj_host: numpy float32 [P][Nv][Nu]; returns a
+    numpy float32 [N][N][N] (or fills `out`).  Device memory holds one band
+    of projections, its filtered rows, its decomposed data and one slab."""
+    import numpy as np
+    import torch
+    N = plan.N
+    if out is None:
+        out = np.empty((N, N, N), dtype=np.float32)
+    bands = [(z0, min(slab, N - z0)) + plan.slab_rows(z0, min(slab, N - z0)) for z0 in range(0, N, slab)]
+    max_rows = max(b[3] for b in bands)
+    S = None
+    if plan.D > 1:
+        S = torch.empty(plan.slab_workspace_elems(max_rows), dtype=torch.float32, device="cuda")
+    for z0, nz, v0, nr in bands:
+        rows = torch.from_numpy(np.ascontiguousarray(proj_host[:, v0:v0 + nr, :])).cuda()
+        Q = plan.filter_rows(rows, v0)
+        vol = plan.backproject_slab(Q, v0, S, z0, nz)
+        out[z0:z0 + nz] = vol.cpu().numpy()
+    return out

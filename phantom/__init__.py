@@ -41,6 +41,49 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_SRC_GPU = os.path.join(_HERE, "project_gpu.cu")
+_SO_GPU = os.path.join(_HERE, "_phantom_gpu.so")
+_lib_gpu = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the GPU projector (nvcc, sm_103a) into an in-tree shared object."""
+    if force or not os.path.exists(_SO_GPU) or os.path.getmtime(_SO_GPU) < os.path.getmtime(_SRC_GPU):
+        tmp = _SO_GPU + f".{os.getpid()}.tmp"
+        nvcc = os.environ.get("NVCC") or "nvcc"
+        if not os.path.exists(nvcc) and os.path.exists("/usr/local/cuda/bin/nvcc"):
+            nvcc = "/usr/local/cuda/bin/nvcc"
+        subprocess.check_call([nvcc, "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-Xcompiler", "-fPIC",
+                               "-shared", "-o", tmp, _SRC_GPU])
+        os.replace(tmp, _SO_GPU)
+    return _SO_GPU
+
+
+def project_gpu(ell: np.ndarray, R: float, Nu: int, Nv: int, P: int, out=None, k0: int = 0, k1: int | None = None):
+    """The same line integrals as `project`, computed on the current CUDA
+    device in FP32 (input generation for large workloads); returns a torch
+    float32 tensor [k1-k0][Nv][Nu] on the device."""
+    global _lib_gpu
+    import torch
+    with _lock:
+        if _lib_gpu is None:
+            lib = ctypes.CDLL(build_gpu())
+            lib.phantom_project_gpu.restype = ctypes.c_int
+            lib.phantom_project_gpu.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_void_p, ctypes.c_size_t]
+            _lib_gpu = lib
+    k1 = P if k1 is None else k1
+    e32 = np.ascontiguousarray(ell, dtype=np.float32).reshape(-1, NPAR)
+    if out is None:
+        out = torch.empty((k1 - k0, Nv, Nu), dtype=torch.float32, device="cuda")
+    rc = _lib_gpu.phantom_project_gpu(e32.shape[0], e32.ctypes.data, float(R), Nu, Nv, P, k0, k1,
+                                      out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"GPU projector failed ({rc})")
+    return out
+
+
 def _load():
     global _lib
     with _lock:
@@ -167,6 +210,18 @@ WORKLOADS = {
     "fdkod_1024": Workload("fdkod_1024^3_P720_s4_D8", 1024, 720, 4, 8, 80, 0.0, 3000),
     "fdkod_2000": Workload("fdkod_2000^3_P720_s5_D16", 2000, 720, 5, 16, 150, 0.01, 5000),
 }
+
+
+def batched_workload(seed: int = 4000, count: int = 64, sizes=(64, 96, 128, 192, 256, 384), n_ell: int = 20):
+    """Many volumes of uneven size: N drawn (seeded) from `sizes`,
+    P = round(1.4 N) views, R = 4N, `n_ell` ellipsoids each.
+    Returns a list of (N, P, R, seed_i)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        N = int(rng.choice(sizes))
+        out.append((N, int(round(1.4 * N)), 4.0 * N, seed + 1 + i))
+    return out
 
 
 def make_projections(w: Workload, dtype=np.float32) -> np.ndarray:

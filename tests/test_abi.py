@@ -46,6 +46,11 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     for g, s, D, qt, want in bad:
         assert lib.fdkod_plan(ctypes.byref(g), s, D, qt, ctypes.byref(out)) == want, (g.N, s, D, qt)
         assert out.value is None
+    g = F.Geometry(64.0, 16, 16, 16, 8)
+    assert lib.fdkod_plan_ex(ctypes.byref(g), 1, 1, 0, 2, ctypes.byref(out)) == -1   # unknown flag
+    assert lib.fdkod_slab_rows(None, 0, 1, None, None) == -1
+    assert lib.fdkod_filter_rows(None, None, 0, 1, None, 0) == -1
+    assert lib.fdkod_backproject_slab(None, None, 0, 1, None, 0, 1, None, 0) == -1
     for rc in (0, -1, -2, -3, -4, -5, -6, 99):
         assert lib.fdkod_strerror(rc)
     assert lib.fdkod_filter(None, None, None, 0) == -1

@@ -1,0 +1,67 @@
+"""Batched reconstruction of volumes of uneven size in one CUDA graph, against
+eager launches (bit for bit) and against the FP64 oracle (parity bar)."""
+import numpy as np
+import pytest
+
+import phantom
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fd():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1708_07515_gb300 as fd
+    fd.load()
+    return fd
+
+
+def test_graph_batch_matches_eager_and_oracle(fd, oracle_mod):
+    from paper_1708_07515_gb300.batch import BatchReconstructor, Instance
+    sizes = (32, 40, 48, 64)
+    work = phantom.batched_workload(seed=4100, count=6, sizes=sizes, n_ell=6)
+    insts = [Instance(R, N, N, N, P) for N, P, R, _ in work]
+    projs = [phantom.project(phantom.make_phantom(sd, N, 6), R, N, N, P) for N, P, R, sd in work]
+    br = BatchReconstructor(insts, rates=(1.5e12, 4e11))
+    try:
+        for inst in insts:
+            assert inst.P % inst.D == 0 and 0 <= inst.s <= 7
+        br.load(projs)
+        br.run_eager()
+        torch.cuda.synchronize()
+        eager = [v.clone() for v in br.vol]
+        for v in br.vol:
+            v.fill_(float("nan"))
+        br.capture()
+        br.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(eager, br.vol):
+            assert torch.equal(a, b)
+        for inst, p, v in zip(insts, projs, br.vol):
+            Q = oracle_mod.filter(p, inst.R)
+            want = oracle_mod.fdkod(Q, inst.R, inst.N, inst.s, inst.D)
+            got = v.cpu().numpy().astype(np.float64)
+            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert rel <= 1e-5, (inst, rel)
+        assert all(p.device_status() == 0 for p in br.plans)
+    finally:
+        br.close()
+
+
+def test_measured_rates_are_positive(fd):
+    from paper_1708_07515_gb300 import autotune
+    bp, dec = autotune.measure_rates(N=64, P=60)
+    assert bp > 1e9 and dec > 1e8
+
+
+def test_gpu_projector_matches_cpu_projector(fd):
+    """Input generation for large workloads: the GPU projector (FP32) agrees
+    with the FP64 CPU projector."""
+    N, P = 96, 24
+    R = 4.0 * N
+    ell = phantom.make_phantom(4242, N, 20)
+    cpu = phantom.project(ell, R, N + 4, N - 6, P, dtype=np.float64)
+    gpu = phantom.project_gpu(ell, R, N + 4, N - 6, P).cpu().numpy().astype(np.float64)
+    assert np.abs(gpu - cpu).max() <= 2e-5 * np.abs(cpu).max()
