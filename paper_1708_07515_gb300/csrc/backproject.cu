@@ -279,8 +279,9 @@ struct Lds<__half, OFF> {
 constexpr int kMagicBits = 0x4B400000;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
+// three CTAs per SM (the shared-memory limit): up to 80 registers per thread
 template <typename TS, bool DIRECT, int WD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     constexpr int ES = (int)sizeof(TS);      // window element size (bytes)
     constexpr int kAl = 16 / ES;             // copy start alignment (elements)
