@@ -244,8 +244,9 @@ def batched_main(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (projections generated on the GPU)",
            "config": {"workload": "batched_64_volumes_N64-384_P1.4N", "volumes": len(insts),
                       "step": "one CUDA-graph launch: bounds + filter + decompose + backproject of every volume",
+                      "streams": len(br.lanes),
                       "choices": [[i.N, i.P, i.s, i.D] for i in insts], "rates": list(rates)},
-           "gpu_launches": 4 * len(insts) * args.steps, "clocks": clk.summary()}
+           "gpu_launches": br.launches() * args.steps, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
     br.close()
     return 0

@@ -4,8 +4,11 @@ Each volume gets its own plan (s and D chosen by the autotuner from the
 Eq. 4-6 cost model with this GPU's measured rates), its own device buffers,
 and the four stages of the hot path (bounds, filter, decomposition,
 backprojection) for every volume are captured once into a single CUDA graph;
-a batch then runs as one graph launch.  All kernels are libfdkod's; torch
-only provides memory, streams and the graph object.
+a batch then runs as one graph launch.  Volumes are independent, so they are
+spread over several streams (largest estimated cost first, each to the
+least-loaded stream): in the graph they become parallel branches and small
+volumes fill the SMs that a large one leaves idle.  All kernels are
+libfdkod's; torch only provides memory, streams and the graph object.
 """
 from __future__ import annotations
 
@@ -13,6 +16,23 @@ from dataclasses import dataclass
 
 from . import autotune
 from .fdkod import Plan
+
+
+def work_estimate(inst) -> float:
+    """Relative cost of one volume: its backprojection updates N^3 P / D."""
+    return float(inst.N) ** 3 * inst.P / max(1, inst.D)
+
+
+def assign_lanes(costs: list[float], lanes: int) -> list[int]:
+    """Longest-processing-time-first: each volume, largest first, goes to the
+    lane with the least work so far.  Returns the lane of every volume."""
+    load = [0.0] * lanes
+    out = [0] * len(costs)
+    for k in sorted(range(len(costs)), key=lambda i: -costs[i]):
+        j = min(range(lanes), key=lambda i: load[i])
+        out[k] = j
+        load[j] += costs[k]
+    return out
 
 
 @dataclass
@@ -28,7 +48,7 @@ class Instance:
 
 class BatchReconstructor:
     def __init__(self, instances: list[Instance], qtype: str = "f32", rates: tuple[float, float] | None = None,
-                 skip: int = 0):
+                 skip: int = 0, streams: int = 4):
         import torch
         self.torch = torch
         self.instances = instances
@@ -47,27 +67,42 @@ class BatchReconstructor:
             self.vol.append(torch.empty((inst.N, inst.N, inst.N), dtype=torch.float32, device="cuda"))
         self.graph = None
         self.stream = torch.cuda.Stream()
+        self.lanes = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        self.assign = assign_lanes([work_estimate(i) for i in instances], len(self.lanes))
 
-    def _enqueue(self, stream_handle: int):
-        for plan, p, Q, v in zip(self.plans, self.proj, self.Q, self.vol):
-            plan.compute_bounds(stream_handle)
-            plan.filter(p, Q, stream_handle)
-            plan.backproject(Q, v, stream_handle)
+    def launches(self) -> int:
+        """Kernel launches per batch: bounds, filter, and the decomposition
+        (only when D > 1) plus the backprojection of every volume."""
+        return sum(4 if i.D > 1 else 3 for i in self.instances)
+
+    def _enqueue(self, main):
+        """Every volume's stages on its lane; the lanes fork from and join
+        back into `main` (in a capture they become parallel graph branches)."""
+        for lane in self.lanes:
+            lane.wait_stream(main)
+        for k, (plan, p, Q, v) in enumerate(zip(self.plans, self.proj, self.Q, self.vol)):
+            h = int(self.lanes[self.assign[k]].cuda_stream)
+            plan.compute_bounds(h)
+            plan.filter(p, Q, h)
+            plan.backproject(Q, v, h)
+        for lane in self.lanes:
+            main.wait_stream(lane)
 
     def run_eager(self):
-        """All stages launched one by one on the current stream."""
-        self._enqueue(int(self.torch.cuda.current_stream().cuda_stream))
+        """All stages launched one by one (forked over the lanes from the
+        current stream and joined back into it)."""
+        self._enqueue(self.torch.cuda.current_stream())
 
     def capture(self):
         """Record the whole batch into one CUDA graph (after one eager run,
         which sets the kernels' shared-memory attributes outside capture)."""
         torch = self.torch
         with torch.cuda.stream(self.stream):
-            self._enqueue(int(self.stream.cuda_stream))
+            self._enqueue(self.stream)
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=self.stream):
-            self._enqueue(int(self.stream.cuda_stream))
+            self._enqueue(self.stream)
         self.graph = g
         return g
 

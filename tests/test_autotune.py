@@ -46,3 +46,15 @@ def test_measured_search_keeps_the_fastest():
     c = autotune.choose(256, 360, 1.5e12, 4e11, timer=timer)
     assert c.measured_ms == min(10.0 + (s - 2) ** 2 for s, _ in calls)
     assert len(calls) <= 3
+
+
+def test_lane_assignment_balances_longest_first():
+    from paper_1708_07515_gb300.batch import assign_lanes
+    costs = [5.0, 1.0, 4.0, 3.0, 3.0, 2.0]
+    lanes = assign_lanes(costs, 2)
+    assert lanes == [0, 0, 1, 1, 0, 1]
+    load = [sum(c for c, l in zip(costs, lanes) if l == j) for j in range(2)]
+    assert max(load) - min(load) <= max(costs)
+    # one lane: everything on it; more lanes than volumes: one volume each
+    assert assign_lanes(costs, 1) == [0] * 6
+    assert sorted(assign_lanes(costs[:3], 5)) == [0, 1, 2]
