@@ -127,6 +127,8 @@ FDKOD_CASES = [
     (64, 64, 2, 1, 64, 64, 4.0),       # D = 1: crop only
     (40, 48, 0, 2, 41, 41, 4.0),       # s = 0
     (64, 32, 2, 32, 64, 64, 4.0),      # one decimated view
+    (96, 64, 1, 4, 100, 90, 4.0),      # decomposed rows of 65..128 columns (32 lanes per row)
+    (96, 48, 0, 2, 96, 96, 4.0),       # rows past 128 columns (8 columns per lane)
 ]
 
 
@@ -141,7 +143,7 @@ def test_fdkod_parity(fd, oracle_mod, N, P, s, D, Nu, Nv, Rf):
     plan.close()
 
 
-@pytest.mark.parametrize("N,P,s,D", [(64, 96, 3, 4), (50, 60, 2, 3), (32, 32, 1, 2)])
+@pytest.mark.parametrize("N,P,s,D", [(64, 96, 3, 4), (50, 60, 2, 3), (32, 32, 1, 2), (96, 48, 0, 2), (96, 64, 1, 4)])
 def test_decomposed_data_parity(fd, oracle_mod, N, P, s, D):
     _, Q, R = _q_from_phantom(oracle_mod, N, P, 6, 400 + N)
     plan = fd.Plan(R, N, N, N, P, s, D)
@@ -193,7 +195,8 @@ def _round16(Q, qtype):
 
 
 @pytest.mark.parametrize("qtype", ["bf16", "f16"])
-@pytest.mark.parametrize("N,P,s,D,Nu,Nv", [(64, 96, 3, 4, 64, 64), (50, 60, 2, 3, 53, 47)])
+@pytest.mark.parametrize("N,P,s,D,Nu,Nv", [(64, 96, 3, 4, 64, 64), (50, 60, 2, 3, 53, 47), (128, 128, 2, 2, 128, 128),
+                                            (96, 64, 1, 4, 96, 96), (96, 48, 0, 2, 96, 96)])
 def test_precision_forms_parity_on_identical_inputs(fd, oracle_mod, qtype, N, P, s, D, Nu, Nv):
     """Both sides read the same 16-bit-rounded Q; the arithmetic is FP32 on
     the GPU and FP64 in the oracle, so the FP32 bar applies."""
