@@ -14,6 +14,7 @@ Functions and the passages they follow:
   bounds                 Eq. 1 at the four vertices of each square (Sec. 2.1)
                          for the 4^s squares of Sec. 2.2
   shift_decimate         shift + angular low-pass + downsample (Sec. 2.1)
+  triangle_taps / sinc_taps   the angular low-pass kernels (default / windowed sinc)
   fdkod / fdkod_slices   FDK-OD (Sec. 2.2)
 
 Every function here has at least one pin in tests/test_oracle_*.py that does
@@ -66,11 +67,11 @@ def _load():
                 "oracle_bounds": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _vp,
                                            _vp]),
                 "oracle_shift_decimate": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp,
-                                                   _c_int, _c_int, _vp]),
+                                                   _c_int, _c_int, _vp, _vp, _c_int]),
                 "oracle_fdkod_slices": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp,
-                                                 _c_int, _c_int, _vp, _vp]),
+                                                 _c_int, _c_int, _vp, _vp, _vp, _c_int]),
                 "oracle_fdkod": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int,
-                                          _vp]),
+                                          _vp, _vp, _c_int]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -178,29 +179,61 @@ def bounds(R: float, N: int, Nu: int, P: int, s: int) -> dict:
     return {"lo": lo, "hi": hi, "crop": crop, "phi": phi, "w0": w0, "T": T}
 
 
-def shift_decimate(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int) -> np.ndarray:
-    """Decomposed data S'_q[j][v][t] of square q (D > 1)."""
+def triangle_taps(D: int) -> np.ndarray:
+    """The default angular low-pass of Sec. 2.1 (its kernel is left open; the
+    reading here is the triangle): h[|i|] = (D - |i|) / D^2, |i| < D."""
+    i = np.arange(D, dtype=np.float64)
+    return (D - i) / float(D * D)
+
+
+def sinc_taps(D: int, H: int = 2) -> np.ndarray:
+    """Hann-windowed sinc low-pass with its cutoff at the decimated Nyquist
+    frequency pi / D (Sec. 2.1 says the low-pass filter sets the quality):
+    g_i = sinc(i / D) (1 + cos(pi i / (H D))) / 2 for |i| < H D, scaled to
+    unit gain at zero frequency.  Returns h[|i|], |i| = 0 .. H D - 1."""
+    i = np.arange(H * D, dtype=np.float64)
+    g = np.sinc(i / D) * 0.5 * (1.0 + np.cos(np.pi * i / (H * D)))
+    return g / (g[0] + 2.0 * g[1:].sum())
+
+
+def _taps_arg(taps, D: int):
+    """(pointer, H) for the C oracle: None is the triangle."""
+    if taps is None:
+        return None, 1, None
+    h = np.ascontiguousarray(taps, dtype=np.float64).reshape(-1)
+    if h.size % D != 0 or h.size == 0:
+        raise ValueError("taps must hold H D values h[0 .. H D - 1]")
+    return _ptr(h), h.size // D, h
+
+
+def shift_decimate(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, taps=None) -> np.ndarray:
+    """Decomposed data S'_q[j][v][t] of square q (D > 1); taps: h[|i|] of
+    the angular low-pass (None: the triangle)."""
     Q, f64 = _qarg(Q)
     P, Nv, Nu = Q.shape
     T = int(bounds(R, N, Nu, P, s)["T"][q])
     out = np.empty((P // D, Nv, T), dtype=np.float64)
-    _check(_load().oracle_shift_decimate(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, q, _ptr(out)), "shift_decimate")
+    hp, H, _keep = _taps_arg(taps, D)
+    _check(_load().oracle_shift_decimate(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, q, _ptr(out), hp, H),
+           "shift_decimate")
     return out
 
 
-def fdkod_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, zs) -> np.ndarray:
+def fdkod_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, zs, taps=None) -> np.ndarray:
     Q, f64 = _qarg(Q)
     P, Nv, Nu = Q.shape
     zs = np.ascontiguousarray(zs, dtype=np.int32).reshape(-1)
     out = np.empty((zs.size, N, N), dtype=np.float64)
-    _check(_load().oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, zs.size, _ptr(zs), _ptr(out)),
+    hp, H, _keep = _taps_arg(taps, D)
+    _check(_load().oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, zs.size, _ptr(zs), _ptr(out), hp, H),
            "fdkod_slices")
     return out
 
 
-def fdkod(Q: np.ndarray, R: float, N: int, s: int, D: int) -> np.ndarray:
+def fdkod(Q: np.ndarray, R: float, N: int, s: int, D: int, taps=None) -> np.ndarray:
     Q, f64 = _qarg(Q)
     P, Nv, Nu = Q.shape
     out = np.empty((N, N, N), dtype=np.float64)
-    _check(_load().oracle_fdkod(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, _ptr(out)), "fdkod")
+    hp, H, _keep = _taps_arg(taps, D)
+    _check(_load().oracle_fdkod(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, _ptr(out), hp, H), "fdkod")
     return out

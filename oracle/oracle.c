@@ -28,7 +28,9 @@
  *    phi_k = a(x_c, y_c, beta_k) + (Nu-1)/2;
  *  - angular decimation: triangle low-pass with taps (D - |i|) / D^2,
  *    |i| < D, circular over the full orbit, then keep every D-th angle
- *    (Sec. 2.1: low-pass filter, then downsample);
+ *    (Sec. 2.1: low-pass filter, then downsample).  Sec. 2.1 leaves the
+ *    filter open (its quality "can be adjusted"), so any symmetric taps
+ *    h[|i|], |i| < H D, may be passed instead (h = NULL: the triangle);
  *  - the second shift back to original positions is folded into the
  *    backprojection's column coordinate (Sec. 2.2 says FDK-OD performs a
  *    single interpolation);
@@ -303,6 +305,8 @@ int oracle_bounds(double R, int N, int Nu, int P, int s, int32_t *lo, int32_t *h
 typedef struct {
     double R;
     int N, Nu, Nv, P, s, D, Pd;
+    const double *h; /* angular taps h[|i|], |i| < H D; NULL: triangle */
+    int H;
     int nsq;       /* 4^s */
     double *phi;   /* [nsq][P] */
     int32_t *lo, *hi, *w0, *T;
@@ -316,9 +320,13 @@ static void odplan_free(odplan *o) {
     free(o->T);
 }
 
-static int odplan_make(odplan *o, double R, int N, int Nu, int Nv, int P, int s, int D) {
+static int odplan_make(odplan *o, double R, int N, int Nu, int Nv, int P, int s, int D, const double *h,
+                       int H) {
     memset(o, 0, sizeof(*o));
     if (D <= 0 || P <= 0 || P % D != 0) return ORACLE_EINVAL;
+    if (H < 1 || (h == NULL && H != 1)) return ORACLE_EINVAL;
+    o->h = h;
+    o->H = H;
     if (s < 0 || s > 20 || (1L << s) > N) return ORACLE_EINVAL;
     o->R = R;
     o->N = N;
@@ -357,7 +365,7 @@ static double lerp_row(qbuf Q, size_t off, int Nu, double pos) {
  *   1. shift: S[k][t] = Q_k(v, phi_k + w0 + t), t = 0..T-1, which puts the
  *      square centre on one column for every angle;
  *   2. low-pass along the angle axis: F[k][t] = sum_i h_i S[(k+i) mod P][t],
- *      h_i = (D - |i|) / D^2 for |i| < D;
+ *      h_i = (D - |i|) / D^2 for |i| < D (or the given taps, |i| < H D);
  *   3. downsample: S'[j][t] = F[j D][t], j = 0..P/D-1.
  * out[j][t] has row stride T (one row v only). */
 static void shift_decimate_row(const odplan *o, qbuf Q, int q, int v, double *S, double *out) {
@@ -370,9 +378,10 @@ static void shift_decimate_row(const odplan *o, qbuf Q, int q, int v, double *S,
     for (int j = 0; j < o->Pd; ++j) {
         for (int t = 0; t < T; ++t) {
             double acc = 0.0;
-            for (int i = -(D - 1); i <= D - 1; ++i) {
+            int half = o->H * D;
+            for (int i = -(half - 1); i <= half - 1; ++i) {
                 int k = ((j * D + i) % P + P) % P;
-                double h = (double)(D - abs(i)) / ((double)D * (double)D);
+                double h = o->h ? o->h[abs(i)] : (double)(D - abs(i)) / ((double)D * (double)D);
                 acc += h * S[(size_t)k * T + t];
             }
             out[(size_t)j * T + t] = acc;
@@ -383,10 +392,10 @@ static void shift_decimate_row(const odplan *o, qbuf Q, int q, int v, double *S,
 /* Decomposed data S'_q[j][v][t] of one square (all detector rows), for
  * inspecting the shift/decimation stage on its own.  D > 1 only. */
 int oracle_shift_decimate(double R, int N, int Nu, int Nv, int P, int s, int D,
-                          const void *Q, int q_f64, int q, double *out) {
+                          const void *Q, int q_f64, int q, double *out, const double *h, int H) {
     if (D < 2) return ORACLE_EINVAL;
     odplan o;
-    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D);
+    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D, h, H);
     if (rc) return rc;
     if (q < 0 || q >= o.nsq) {
         odplan_free(&o);
@@ -424,12 +433,12 @@ int oracle_shift_decimate(double R, int N, int Nu, int Nv, int P, int s, int D,
  *          the P/D angles beta_{jD}, with scale pi / (P/D) and column
  *          coordinate t = u - phi - w0 (the shift back folded in). */
 int oracle_fdkod_slices(double R, int N, int Nu, int Nv, int P, int s, int D,
-                        const void *Q, int q_f64, int nz, const int *zs, double *vol) {
+                        const void *Q, int q_f64, int nz, const int *zs, double *vol, const double *h, int H) {
     if (nz < 0) return ORACLE_EINVAL;
     for (int i = 0; i < nz; ++i)
         if (zs[i] < 0 || zs[i] >= N) return ORACLE_EINVAL;
     odplan o;
-    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D);
+    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D, h, H);
     if (rc) return rc;
     qbuf qb = {Q, q_f64};
     const double uc = 0.5 * (double)(Nu - 1), vc = 0.5 * (double)(Nv - 1);
@@ -544,11 +553,11 @@ int oracle_fdkod_slices(double R, int N, int Nu, int Nv, int P, int s, int D,
 }
 
 int oracle_fdkod(double R, int N, int Nu, int Nv, int P, int s, int D, const void *Q,
-                 int q_f64, double *vol) {
+                 int q_f64, double *vol, const double *h, int H) {
     int *zs = (int *)malloc(sizeof(int) * (size_t)N);
     if (!zs) return ORACLE_ENOMEM;
     for (int i = 0; i < N; ++i) zs[i] = i;
-    int rc = oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, Q, q_f64, N, zs, vol);
+    int rc = oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, Q, q_f64, N, zs, vol, h, H);
     free(zs);
     return rc;
 }
