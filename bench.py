@@ -60,6 +60,8 @@ def parse():
                     help="64 volumes of uneven size (N in {64..384}, P = 1.4 N) in one CUDA graph")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the filtered projections (arithmetic stays float32)")
+    ap.add_argument("--taps", choices=["triangle", "sinc"], default="triangle",
+                    help="angular low-pass of the decomposition (Sec. 2.1): triangle or Hann-windowed sinc")
     return ap.parse_args()
 
 
@@ -291,7 +293,7 @@ def main():
         if w.noise:
             phantom.add_noise(proj, w.noise, w.seed + rank)
 
-    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype)
+    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=args.taps)
     info = plan.info
     stream = torch.cuda.current_stream()
     proj_d = torch.from_numpy(proj).cuda()
@@ -425,7 +427,8 @@ def main():
         Qo = np.zeros((w.P, w.Nv, w.Nu))
         Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
         ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
-        ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs)
+        ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
+                                     taps=oracle.sinc_taps(w.D) if args.taps == "sinc" else None)
         g = vol_od[zs].astype(np.float64)
         extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(g - ref_od) / np.linalg.norm(ref_od))
         extra["rel_rmse_vs_fp64_fdk_oracle"] = float(np.linalg.norm(g - ref_fdk) / np.linalg.norm(ref_fdk))
@@ -461,7 +464,8 @@ def main():
                      + (f", {100 * w.noise:g}% Gaussian noise" if w.noise else "")
                      + (" (projections generated on the GPU)" if gpu_inputs else "")),
             "config": {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s,
-                       "D": w.D, "q_storage": args.qtype, "step": "bounds + filter + decompose + backproject",
+                       "D": w.D, "q_storage": args.qtype, "taps": args.taps,
+                       "step": "bounds + filter + decompose + backproject",
                        "l2": f"inputs larger than L2 (projections {proj.nbytes / 1e6:.0f} MB, decomposed data "
                              f"{info['decomposed_elems'] * 4 / 1e9:.2f} GB)",
                        "parallelism": f"{world} independent scans, one per GPU"},

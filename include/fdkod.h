@@ -99,13 +99,18 @@ int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_p
 
 /* Flags of fdkod_plan_ex. */
 #define FDKOD_PLAN_NO_WORKSPACE 1 /* do not allocate the whole-volume decomposed-data workspace */
+#define FDKOD_PLAN_SINC_TAPS 2    /* windowed-sinc angular low-pass instead of the triangle */
 
 /*
  * fdkod_plan with flags.  FDKOD_PLAN_NO_WORKSPACE leaves out the
  * 4^s * (P/D) * Nv * T_stride float workspace of fdkod_backproject: such a
  * plan serves the slab-wise entry points below (piecemeal reconstruction,
  * Sec. 2.2), and fdkod_backproject then returns FDKOD_ERR_INVALID_ARG when
- * D > 1.  Other flags: INVALID_ARG.  Otherwise as fdkod_plan.
+ * D > 1.  FDKOD_PLAN_SINC_TAPS selects the Hann-windowed sinc of
+ * fdkod_sinc_taps with H = 2 as the angular low-pass of the decomposition
+ * (Sec. 2.1 leaves the filter open; the default is the triangle
+ * (D - |i|) / D^2, |i| < D).  Other flags: INVALID_ARG.  Otherwise as
+ * fdkod_plan; D above 128 is UNSUPPORTED.
  */
 int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int flags, fdkod_plan_t **out);
 
@@ -265,6 +270,29 @@ int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
  */
 int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, const float *Q, float *vol,
                               uintptr_t stream);
+
+/*
+ * Angular low-pass of the decomposition (Sec. 2.1: low-pass filter over the
+ * angles, then keep every D-th).  The filter is symmetric and circular over
+ * the orbit: decimated view j is sum_i h[|i|] S[(jD + i) mod P], |i| < n,
+ * with n = D (support of the triangle) or n = 2D.
+ *
+ * fdkod_set_decimation_taps: copy h[0 .. n-1] (host, not retained) into
+ *   the plan; n must be D or 2D and the plan must have D > 1.  Synchronous;
+ *   call it while no launch of this plan is in flight.  The taps are used as
+ *   given (scale them to unit sum for unit gain).  Errors: INVALID_ARG
+ *   (n, D, non-finite values), CUDA.
+ * fdkod_get_decimation_taps: the plan's n taps into h[0 .. min(n, cap)-1];
+ *   returns n (>= 1) or INVALID_ARG.
+ * fdkod_sinc_taps: host only, no device work: the Hann-windowed sinc with
+ *   its cutoff at the decimated Nyquist frequency pi / D,
+ *   g_i = sinc(i / D) (1 + cos(pi i / (H D))) / 2 for |i| < H D, scaled to
+ *   unit sum, into h[0 .. H D - 1].  H is 1 or 2.  Errors: INVALID_ARG
+ *   (D < 1 or above 128, H outside 1..2, h NULL).
+ */
+int fdkod_set_decimation_taps(fdkod_plan_t *plan, const double *h, int n);
+int fdkod_get_decimation_taps(const fdkod_plan_t *plan, double *h, int cap);
+int fdkod_sinc_taps(int D, int H, double *h);
 
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);

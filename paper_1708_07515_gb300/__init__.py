@@ -19,7 +19,10 @@ from .fdkod import (  # noqa: F401
     fdkod_decompose,
     fdkod_filter,
     fdkod_get_bounds,
+    fdkod_get_decimation_taps,
     fdkod_plan,
+    fdkod_set_decimation_taps,
+    fdkod_sinc_taps,
     lib_path,
     load,
     reconstruct_slabs,

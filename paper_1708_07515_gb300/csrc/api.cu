@@ -1,6 +1,7 @@
 // C ABI of libfdkod: plan construction (host-side validation, trig tables,
 // FFT tables, workspace sizing) and the entry points of include/fdkod.h.
 #include <math.h>
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
@@ -53,6 +54,7 @@ void free_plan(PlanImpl &p) {
     cudaFree(p.H);
     cudaFree(p.tw);
     cudaFree(p.Sp);
+    cudaFree(p.tapw);
     cudaFree(p.status);
 }
 
@@ -120,6 +122,35 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     for (int w : {128, 96, 64, 48, 32}) {
         if (need <= w) ss.WdT = w;
         if (need16 <= w) ss.WdT16 = w;
+    }
+}
+
+void triangle_taps(int D, double *h) {
+    for (int i = 0; i < D; ++i) h[i] = (double)(D - i) / ((double)D * (double)D);
+}
+
+void sinc_taps(int D, int H, double *h) {
+    // g_i = sinc(i / D) (1 + cos(pi i / (H D))) / 2, |i| < H D, scaled so the
+    // two-sided sum (the response at zero frequency) is 1
+    const int n = H * D;
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = (double)i / (double)D;
+        const double sinc = i == 0 ? 1.0 : sin(M_PI * x) / (M_PI * x);
+        h[i] = sinc * 0.5 * (1.0 + cos(M_PI * (double)i / (double)n));
+        sum += i == 0 ? h[i] : 2.0 * h[i];
+    }
+    for (int i = 0; i < n; ++i) h[i] /= sum;
+}
+
+void tap_table(const double *h, int H, int D, float4 *w) {
+    for (int r = 0; r < D; ++r) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int m = 0; m < 2 * H; ++m) {
+            const int o = std::abs(r + (H - 1 - m) * D);
+            v[m] = o < H * D ? (float)h[o] : 0.f;
+        }
+        w[r] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -213,6 +244,16 @@ int build_plan(PlanImpl &p, cudaStream_t st) {
     rc = make_fft_tables(p, st);
     if (rc) return rc;
     p.Tstride = (p.od.Tmax + 3) & ~3;
+    // angular low-pass of the decomposition
+    if (p.tap_blocks == 2) sinc_taps(p.D, 2, p.htaps);
+    else triangle_taps(p.D, p.htaps);
+    {
+        std::vector<float4> w(p.D);
+        tap_table(p.htaps, p.tap_blocks, p.D, w.data());
+        FDKOD_TRY(dalloc(p, &p.tapw, (size_t)p.D));
+        FDKOD_TRY(cudaMemcpyAsync(p.tapw, w.data(), sizeof(float4) * p.D, cudaMemcpyHostToDevice, st));
+        FDKOD_TRY(cudaStreamSynchronize(st));
+    }
     if (p.D > 1 && !p.no_workspace) {
         p.sp_elems = (int64_t)p.od.nsq * p.Pd * p.g.Nv * p.Tstride;
         FDKOD_TRY(dalloc(p, &p.Sp, (size_t)p.sp_elems));
@@ -266,7 +307,7 @@ int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_p
 int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int flags, fdkod_plan_t **out) {
     if (!g || !out) return FDKOD_ERR_INVALID_ARG;
     *out = nullptr;
-    if (flags & ~FDKOD_PLAN_NO_WORKSPACE) return FDKOD_ERR_INVALID_ARG;
+    if (flags & ~(FDKOD_PLAN_NO_WORKSPACE | FDKOD_PLAN_SINC_TAPS)) return FDKOD_ERR_INVALID_ARG;
     if (!(g->R > 0.0) || g->N <= 0 || g->Nu <= 0 || g->Nv <= 0 || g->P <= 0 || D <= 0 || !valid_dtype(qtype))
         return FDKOD_ERR_INVALID_ARG;
     const int lim = 1 << 15;
@@ -274,7 +315,7 @@ int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int 
     // the filter's shared-memory FFT holds two buffers of 2^ceil(log2(2 Nu))
     // complex floats and uses one thread per 4 samples (at most 1024)
     if (g->Nu > 2048) return FDKOD_ERR_UNSUPPORTED;
-    if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0) return FDKOD_ERR_UNSUPPORTED;
+    if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0 || D > fdkod::kMaxTapD) return FDKOD_ERR_UNSUPPORTED;
     // the source must lie outside the volume's circumscribed cylinder
     if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;
     fdkod_plan_t *pl = new (std::nothrow) fdkod_plan_t;
@@ -286,6 +327,7 @@ int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int 
     p.Pd = g->P / D;
     p.qtype = qtype;
     p.no_workspace = (flags & FDKOD_PLAN_NO_WORKSPACE) != 0;
+    p.tap_blocks = (flags & FDKOD_PLAN_SINC_TAPS) && D > 1 ? 2 : 1;
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         delete pl;
@@ -442,6 +484,35 @@ int fdkod_backproject_slab(fdkod_plan_t *plan, const void *Q_rows, int v0, int n
     if (p.D == 1) return cuda_status(launch_backproject(p, p.od, true, Q_rows, vol_slab, st, b));
     FDKOD_TRY(launch_decompose(p, Q_rows, S_work, st, b));
     return cuda_status(launch_backproject(p, p.od, false, S_work, vol_slab, st, b));
+}
+
+int fdkod_set_decimation_taps(fdkod_plan_t *plan, const double *h, int n) {
+    if (!plan || !h) return FDKOD_ERR_INVALID_ARG;
+    PlanImpl &p = plan->impl;
+    if (p.D < 2 || (n != p.D && n != 2 * p.D)) return FDKOD_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(h[i])) return FDKOD_ERR_INVALID_ARG;
+    std::vector<float4> w(p.D);
+    tap_table(h, n / p.D, p.D, w.data());
+    if (cudaMemcpy(p.tapw, w.data(), sizeof(float4) * p.D, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FDKOD_ERR_CUDA;
+    p.tap_blocks = n / p.D;
+    for (int i = 0; i < 2 * fdkod::kMaxTapD; ++i) p.htaps[i] = i < n ? h[i] : 0.0;
+    return FDKOD_OK;
+}
+
+int fdkod_get_decimation_taps(const fdkod_plan_t *plan, double *h, int cap) {
+    if (!plan || (cap > 0 && !h)) return FDKOD_ERR_INVALID_ARG;
+    const PlanImpl &p = plan->impl;
+    const int n = p.tap_blocks * p.D;
+    for (int i = 0; i < n && i < cap; ++i) h[i] = p.htaps[i];
+    return n;
+}
+
+int fdkod_sinc_taps(int D, int H, double *h) {
+    if (D < 1 || H < 1 || H > 2 || D > fdkod::kMaxTapD || !h) return FDKOD_ERR_INVALID_ARG;
+    sinc_taps(D, H, h);
+    return FDKOD_OK;
 }
 
 const char *fdkod_strerror(int status) {

@@ -2,13 +2,15 @@
 // v and shifted column t, shift each view's row so the square centre sits
 // on one column (linear interpolation at column phi_k + w0 + t, i.e. crop
 // column c_qk + t with sub-pixel part f_qk), low-pass it along the view
-// axis with the triangle taps (D - |i|) / D^2 (circular over the orbit) and
-// keep every D-th view.  One thread owns one (q, v, t) and streams the P
-// views in order: view k = jD + r adds (D - r) / D^2 of its sample to
-// decimated view j and r / D^2 to view j + 1, so only two running sums are
-// live.  Consecutive threads take consecutive t, so each view's crop row
-// is read as one coalesced segment; CTAs of all squares for the same rows
-// run together and share those rows through L2.
+// axis with symmetric taps h[|i|], |i| < H D (circular over the orbit; the
+// triangle (D - |i|) / D^2 with H = 1 by default, a windowed sinc with
+// H = 2 as an option) and keep every D-th view.  The views are streamed in
+// order: view k = jD + r adds w[r][m] = h[|r + (H - 1 - m) D|] of its sample
+// to decimated view j - H + 1 + m, m < 2H, so only 2H running sums are live
+// (two for the triangle: (D - r) / D^2 to view j, r / D^2 to view j + 1).
+// The stream starts H D - 1 views before view 0 and runs (H - 1) D views
+// past the last one (both wrapped): every decimated view sees its whole
+// support.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -26,11 +28,16 @@ __device__ __forceinline__ float ld_q(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_q(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
 __device__ __forceinline__ float ld_q(const __half *p) { return __half2float(__ldg(p)); }
 
-template <typename TQ>
+// floor(a / b) for b > 0
+__host__ __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Generic path: one thread per (q, v, t), consecutive threads on consecutive
+// t (each view's crop row is one coalesced segment).
+template <typename TQ, int H>
 __global__ void __launch_bounds__(kTX *kTY)
 decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t *__restrict__ crop,
-                 const GeomEntry *__restrict__ geo, const int32_t *__restrict__ Tq, int Tstride, int P, int D,
-                 int Pd, int Nv, int Nu) {
+                 const GeomEntry *__restrict__ geo, const int32_t *__restrict__ Tq, const float4 *__restrict__ tapw,
+                 int Tstride, int P, int D, int Pd, int Nv, int Nu) {
     const int t = blockIdx.x * kTX + threadIdx.x;
     const int v = blockIdx.y * kTY + threadIdx.y;
     const int q = blockIdx.z;
@@ -52,19 +59,30 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
         const float b = (c + 1 >= 0 && c + 1 < Nu) ? ld_q(r + c + 1) : 0.f;
         return fmaf(f, b - a, a);
     };
-    const float inv = 1.0f / (float)(D * D);
-    // the last block of views feeds decimated view 0 (circular orbit)
-    float cur = 0.f, nxt = 0.f;
-    for (int r = 1; r < D; ++r) cur = fmaf((float)r, sample((Pd - 1) * D + r), cur);
-    for (int j = 0; j < Pd; ++j) {
-        for (int r = 0; r < D; ++r) {
-            const float sm = sample(j * D + r);
-            cur = fmaf((float)(D - r), sm, cur);
-            nxt = fmaf((float)r, sm, nxt);
+    float acc[2 * H];
+#pragma unroll
+    for (int m = 0; m < 2 * H; ++m) acc[m] = 0.f;
+    const int nstream = P + (2 * H - 1) * D - 1;
+    const int kp0 = -(H * D - 1);
+    int jb = floor_div(kp0, D), r = kp0 - jb * D, kk = ((kp0 % P) + P) % P;
+    for (int pos = 0; pos < nstream; ++pos) {
+        const float sm = sample(kk);
+        const float4 w = __ldg(tapw + r);
+        const float wm[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int m = 0; m < 2 * H; ++m) acc[m] = fmaf(wm[m], sm, acc[m]);
+        if (r == D - 1) {
+            const int jst = jb - H + 1;  // its support is complete
+            if (jst >= 0) out[(size_t)jst * vstride] = acc[0];
+#pragma unroll
+            for (int m = 0; m < 2 * H - 1; ++m) acc[m] = acc[m + 1];
+            acc[2 * H - 1] = 0.f;
+            r = 0;
+            ++jb;
+        } else {
+            ++r;
         }
-        out[(size_t)j * vstride] = cur * inv;
-        cur = nxt;
-        nxt = 0.f;
+        if (++kk == P) kk = 0;
     }
 }
 
@@ -82,10 +100,11 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
 // consecutive columns t0 .. t0 + C - 1, so one view costs the lane a few
 // vector shared loads at compile-time offsets (the column offset of the
 // crop inside its aligned box selects one of four code paths, uniform per
-// view) and, per column, one lerp and the two tap FMAs.  Everything else
-// a view needs -- shift fraction, which triangle taps apply and whether a
+// view) and, per column, one lerp and the 2H tap FMAs.  Everything else
+// a view needs -- shift fraction, which tap weights apply and whether a
 // decimated view is complete -- is one 8-byte entry of a per-CTA table in
-// stream order, built once from crop[q][.] and frac[q][.].
+// stream order, built once from crop[q][.] and frac[q][.], plus the weights
+// w[r] of its block offset r (one 16-byte entry per r).
 
 constexpr int kConsumerWarps = 8, kG = 4, kStages = 3;
 constexpr int kDecThreads = 32 * (kConsumerWarps + 1);
@@ -94,38 +113,34 @@ constexpr uint64_t kDecWaitNs = 2000000000ull;
 
 // code word of a table entry: bits 0-2 the crop's offset inside its aligned
 // box, bit 3 "last view of a decimated block" (rotate the running sums),
-// bits 4-11 the tap pair, bits 12.. the decimated view to store plus one
-// (0: none, the wrapped block).  D <= 128, so 2D tap pairs fit 8 bits.
+// bits 4-11 the block offset r (its weights), bits 12.. the decimated view
+// to store plus one (0: none, a view before view 0).  D <= 128.
 constexpr int kCodeRotate = 8, kCodeTapShift = 4, kCodeStoreShift = 12;
 
-// Per-CTA tables over the stream positions pos = 0 .. P + D - 2 (view
-// k' = pos - (D - 1), taken mod P): s_fc[pos] = {shift fraction of square q,
-// code word}, s_c[pos] = crop column, and the 2D tap pairs s_taps[r] =
-// (D - r, r) and, for the wrapped block, s_taps[D + r] = (0, r).
+// Per-CTA tables over the stream positions pos = 0 .. P + (2H - 1) D - 2
+// (view k' = pos - (H D - 1), taken mod P): s_fc[pos] = {shift fraction of
+// square q, code word}, s_c[pos] = crop column, and s_taps[r] = the 2H
+// running-sum weights of block offset r (tapw, r < D).
 template <int kAl>
-__device__ __forceinline__ void build_stream_table(float2 *s_fc, int *s_c, float2 *s_taps,
+__device__ __forceinline__ void build_stream_table(float2 *s_fc, int *s_c, float4 *s_taps,
                                                    const int32_t *__restrict__ crop,
-                                                   const GeomEntry *__restrict__ geo, int q, int P, int D) {
-    const int nstream = P + D - 1;
+                                                   const GeomEntry *__restrict__ geo,
+                                                   const float4 *__restrict__ tapw, int q, int P, int D, int Pd,
+                                                   int H) {
+    const int nstream = P + (2 * H - 1) * D - 1;
     for (int pos = threadIdx.x; pos < nstream; pos += blockDim.x) {
-        const int kp = pos - (D - 1);
-        const int kk = kp < 0 ? kp + P : kp;
+        const int kp = pos - (H * D - 1);
+        const int kk = ((kp % P) + P) % P;
         const int c = crop[(size_t)q * P + kk];
-        int j, r;
-        if (kp < 0) {
-            j = -1;
-            r = kp + D;
-        } else {
-            j = kp / D;
-            r = kp - j * D;
-        }
-        int code = (c & (kAl - 1)) | ((j < 0 ? D + r : r) << kCodeTapShift);
-        if (r == D - 1) code |= kCodeRotate | ((j + 1) << kCodeStoreShift);
+        const int jb = floor_div(kp, D);
+        const int r = kp - jb * D;
+        int code = (c & (kAl - 1)) | (r << kCodeTapShift);
+        const int jst = jb - H + 1;  // decimated view whose support ends here
+        if (r == D - 1) code |= kCodeRotate | (jst >= 0 && jst < Pd ? (jst + 1) << kCodeStoreShift : 0);
         s_fc[pos] = make_float2(geo[(size_t)q * P + kk].frac, __int_as_float(code));
         s_c[pos] = c;
     }
-    for (int i = threadIdx.x; i < 2 * D; i += blockDim.x)
-        s_taps[i] = i < D ? make_float2((float)(D - i), (float)i) : make_float2(0.f, (float)(i - D));
+    for (int r = threadIdx.x; r < D; r += blockDim.x) s_taps[r] = tapw[r];
 }
 
 // NV vectors of 4 consecutive elements from 32-bit shared address a, widened to float
@@ -175,9 +190,9 @@ struct VecLoad<__half, NV> {
 };
 
 // One view for one lane: columns t0 + i (i < C) sample the row at box column
-// O + i (+ the shift fraction f) and feed the two running sums.
-template <typename TQ, int C, int O>
-__device__ __forceinline__ void view_cols(uint32_t a, float f, float wa, float wb, float *cur, float *nxt) {
+// O + i (+ the shift fraction f) and feed the 2H running sums with weights w.
+template <typename TQ, int C, int O, int H>
+__device__ __forceinline__ void view_cols(uint32_t a, float f, float4 w, float (*acc)[C]) {
     constexpr int NV = (O + C) / 4 + 1;  // vectors covering elements O .. O + C
     float e[4 * NV];
     VecLoad<TQ, NV>::f(a, e);
@@ -185,31 +200,35 @@ __device__ __forceinline__ void view_cols(uint32_t a, float f, float wa, float w
     for (int i = 0; i < C; ++i) {
         const float a0 = e[O + i], a1 = e[O + i + 1];
         const float smp = fmaf(f, a1 - a0, a0);
-        cur[i] = fmaf(wa, smp, cur[i]);
-        nxt[i] = fmaf(wb, smp, nxt[i]);
+        acc[0][i] = fmaf(w.x, smp, acc[0][i]);
+        acc[1][i] = fmaf(w.y, smp, acc[1][i]);
+        if (H == 2) {
+            acc[2][i] = fmaf(w.z, smp, acc[2][i]);
+            acc[3][i] = fmaf(w.w, smp, acc[3][i]);
+        }
     }
 }
 
 // off: the crop's offset inside its 16-byte aligned box (elements).  For
 // 16-bit data the vectors are 8 bytes, so the lane's address moves by whole
 // vectors and the remainder (0..3) picks the code path.
-template <typename TQ, int C>
-__device__ __forceinline__ void view_step(uint32_t a, int off, float f, float wa, float wb, float *cur, float *nxt) {
+template <typename TQ, int C, int H>
+__device__ __forceinline__ void view_step(uint32_t a, int off, float f, float4 w, float (*acc)[C]) {
     if (sizeof(TQ) == 2) a += 8u * (uint32_t)(off >> 2);
     switch (off & 3) {
-        case 0: view_cols<TQ, C, 0>(a, f, wa, wb, cur, nxt); break;
-        case 1: view_cols<TQ, C, 1>(a, f, wa, wb, cur, nxt); break;
-        case 2: view_cols<TQ, C, 2>(a, f, wa, wb, cur, nxt); break;
-        default: view_cols<TQ, C, 3>(a, f, wa, wb, cur, nxt); break;
+        case 0: view_cols<TQ, C, 0, H>(a, f, w, acc); break;
+        case 1: view_cols<TQ, C, 1, H>(a, f, w, acc); break;
+        case 2: view_cols<TQ, C, 2, H>(a, f, w, acc); break;
+        default: view_cols<TQ, C, 3, H>(a, f, w, acc); break;
     }
 }
 
-template <typename TQ, int C, int LPR>
+template <typename TQ, int C, int LPR, int H>
 __global__ void __launch_bounds__(kDecThreads)
 decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ Sp,
                      const int32_t *__restrict__ crop, const GeomEntry *__restrict__ geo,
-                     const int32_t *__restrict__ Tq, int *status, int Tstride, int P, int D, int Pd, int Nv, int Wc,
-                     int tile_stride) {
+                     const int32_t *__restrict__ Tq, const float4 *__restrict__ tapw, int *status, int Tstride, int P,
+                     int D, int Pd, int Nv, int Wc, int tile_stride) {
     constexpr int ES = (int)sizeof(TQ);
     constexpr int kAlign = 16 / ES;
     constexpr int RPW = 32 / LPR;              // detector rows per consumer warp
@@ -217,20 +236,19 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ring = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     const uint32_t tile_bytes = (uint32_t)(ES * tile_stride);
-    // views streamed: k' = -(D-1) .. P-1 (view k' mod P); the first D-1
-    // (the orbit's last block) only seed decimated view 0
-    const int nstream = P + D - 1;
+    // views streamed: k' = -(H D - 1) .. P - 1 + (H - 1) D (view k' mod P)
+    const int nstream = P + (2 * H - 1) * D - 1;
     const int nstage = (nstream + kG - 1) / kG;
-    float2 *s_fc = (float2 *)(ring + (size_t)tile_bytes * kStages * kG + kRingSlack);
-    float2 *s_taps = s_fc + nstream;
-    int *s_c = (int *)(s_taps + 2 * D);
+    float4 *s_taps = (float4 *)(ring + (size_t)tile_bytes * kStages * kG + kRingSlack);
+    float2 *s_fc = (float2 *)(s_taps + D);
+    int *s_c = (int *)(s_fc + nstream);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
 
     const int q = blockIdx.x;
     const int v0 = blockIdx.y * VB;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 
-    build_stream_table<kAlign>(s_fc, s_c, s_taps, crop, geo, q, P, D);
+    build_stream_table<kAlign>(s_fc, s_c, s_taps, crop, geo, tapw, q, P, D, Pd, H);
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             tma::mbar_init(&full[i], 1);
@@ -242,7 +260,7 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
 
     if (ty == kConsumerWarps) {  // producer
         if (tx != 0) return;
-        int kk = D > 1 ? P - (D - 1) : 0, n = 0, slot = 0;
+        int kk = ((-(H * D - 1)) % P + P) % P, n = 0, slot = 0;
         uint32_t phase = 0;  // parity of the slot's current round
         for (; n < nstage; ++n) {
             // round r of a slot may start once its round r - 1 was consumed
@@ -275,10 +293,11 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     const int T = Tq[q];
     const bool act = t0 < T;
     const bool store = v < Nv && t0 < Tstride;
-    float cur[C], nxt[C];
+    float acc[2 * H][C];
 #pragma unroll
-    for (int i = 0; i < C; ++i) cur[i] = nxt[i] = 0.f;
-    const float inv = 1.0f / (float)(D * D);
+    for (int m = 0; m < 2 * H; ++m)
+#pragma unroll
+        for (int i = 0; i < C; ++i) acc[m][i] = 0.f;
     const size_t vstride = (size_t)Nv * Tstride;
     float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + t0;
     const uint32_t lane_addr = tma::smem_u32(ring) + (uint32_t)(ES * (rib * Wc + t0));
@@ -298,14 +317,14 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
             if (w < nv) {
                 const float2 fc = s_fc[n * kG + w];
                 const int code = __float_as_int(fc.y);
-                const float2 tp = s_taps[(code >> kCodeTapShift) & 255];
-                if (act) view_step<TQ, C>(sa + tile_bytes * (uint32_t)w, code & (kAlign - 1), fc.x, tp.x, tp.y, cur, nxt);
+                const float4 tp = s_taps[(code >> kCodeTapShift) & 255];
+                if (act) view_step<TQ, C, H>(sa + tile_bytes * (uint32_t)w, code & (kAlign - 1), fc.x, tp, acc);
                 if (code & kCodeRotate) {
                     const int jst = (code >> kCodeStoreShift) - 1;
                     if (jst >= 0 && store) {
                         float o[C];
 #pragma unroll
-                        for (int i = 0; i < C; ++i) o[i] = t0 + i < T ? cur[i] * inv : 0.f;
+                        for (int i = 0; i < C; ++i) o[i] = t0 + i < T ? acc[0][i] : 0.f;
                         float4 *dst = (float4 *)(out + (size_t)jst * vstride);
 #pragma unroll
                         for (int i = 0; i < C / 4; ++i)  // Tstride is a multiple of 4
@@ -313,8 +332,9 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                     }
 #pragma unroll
                     for (int i = 0; i < C; ++i) {
-                        cur[i] = nxt[i];
-                        nxt[i] = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 2 * H - 1; ++m) acc[m][i] = acc[m + 1][i];
+                        acc[2 * H - 1][i] = 0.f;
                     }
                 }
             }
@@ -339,17 +359,26 @@ inline DecShape dec_shape(int Tstride) {
     return {8, 32};
 }
 
-template <typename TQ, int C, int LPR>
+template <typename TQ, int C, int LPR, int H>
 cudaError_t launch_tma_shape(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st,
                              int nrows, size_t smem, int tile_stride) {
-    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, LPR>>(smem);
+    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, LPR, H>>(smem);
     if (e != cudaSuccess) return e;
     constexpr int VB = kConsumerWarps * (32 / LPR);
     dim3 grid(p.od.nsq, (nrows + VB - 1) / VB);
-    decompose_tma_kernel<TQ, C, LPR><<<grid, kDecThreads, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T,
-                                                                      p.status, p.Tstride, p.g.P, p.D, p.Pd, nrows,
-                                                                      Wc, tile_stride);
+    decompose_tma_kernel<TQ, C, LPR, H><<<grid, kDecThreads, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T,
+                                                                         p.tapw, p.status, p.Tstride, p.g.P, p.D,
+                                                                         p.Pd, nrows, Wc, tile_stride);
     return cudaGetLastError();
+}
+
+template <typename TQ, int H>
+cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, int nrows,
+                         size_t smem, int tile_stride, DecShape sh) {
+    if (sh.C == 8) return launch_tma_shape<TQ, 8, 32, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
+    if (sh.LPR == 32) return launch_tma_shape<TQ, 4, 32, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
+    if (sh.LPR == 16) return launch_tma_shape<TQ, 4, 16, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
+    return launch_tma_shape<TQ, 4, 8, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
 }
 
 // TMA applies when Q's rows are whole 16-byte units, Q and S' are 16-byte
@@ -362,12 +391,13 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     constexpr int kAlign = 16 / (int)sizeof(TQ);
     if ((p.g.Nu % kAlign) != 0 || ((uintptr_t)Q & 15) != 0 || ((uintptr_t)out & 15) != 0) return cudaSuccess;
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
-    if (Wc > 256 || p.Tstride > 256 || p.D > 128) return cudaSuccess;  // tap pair index: 8 bits
+    if (Wc > 256 || p.Tstride > 256 || p.D > kMaxTapD) return cudaSuccess;  // block offset: 8 bits of the code
     const DecShape sh = dec_shape(p.Tstride);
     const int VB = kConsumerWarps * (32 / sh.LPR);
     const int tile_stride = (VB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
-    const size_t smem = 128 + sizeof(TQ) * (size_t)kStages * kG * tile_stride + kRingSlack +
-                        12 * (size_t)(p.g.P + p.D - 1) + 16 * (size_t)p.D;
+    const int nstream = p.g.P + (2 * p.tap_blocks - 1) * p.D - 1;
+    const size_t smem = 128 + sizeof(TQ) * (size_t)kStages * kG * tile_stride + kRingSlack + 16 * (size_t)p.D +
+                        12 * (size_t)nstream;
     if (smem > 200 * 1024) return cudaSuccess;
     CUtensorMap map;
     const uint64_t dims[3] = {(uint64_t)p.g.Nu, (uint64_t)nrows, (uint64_t)p.g.P};
@@ -378,20 +408,23 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     if (encode_map_3d(&map, dt, Q, dims, strides, box) != cudaSuccess) return cudaSuccess;
     launched = true;
-    if (sh.C == 8) return launch_tma_shape<TQ, 8, 32>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    if (sh.LPR == 32) return launch_tma_shape<TQ, 4, 32>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    if (sh.LPR == 16) return launch_tma_shape<TQ, 4, 16>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    return launch_tma_shape<TQ, 4, 8>(p, map, out, Wc, st, nrows, smem, tile_stride);
+    if (p.tap_blocks == 2) return launch_tma_h<TQ, 2>(p, map, out, Wc, st, nrows, smem, tile_stride, sh);
+    return launch_tma_h<TQ, 1>(p, map, out, Wc, st, nrows, smem, tile_stride, sh);
 }
 
 template <typename TQ>
 cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows) {
+    if (p.tap_blocks != 1 && p.tap_blocks != 2) return cudaErrorInvalidValue;
     bool launched = false;
     cudaError_t te = try_tma(p, Q, out, st, nrows, launched);
     if (launched || te != cudaSuccess) return te;
     dim3 grid((p.Tstride + kTX - 1) / kTX, (nrows + kTY - 1) / kTY, p.od.nsq);
-    decompose_kernel<TQ><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.Tstride, p.g.P,
-                                                          p.D, p.Pd, nrows, p.g.Nu);
+    if (p.tap_blocks == 2)
+        decompose_kernel<TQ, 2><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.tapw,
+                                                                 p.Tstride, p.g.P, p.D, p.Pd, nrows, p.g.Nu);
+    else
+        decompose_kernel<TQ, 1><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.tapw,
+                                                                 p.Tstride, p.g.P, p.D, p.Pd, nrows, p.g.Nu);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ constexpr int kTile = 16;      // tile side in x and y (threads per CTA = 256)
 constexpr int kZT = 32;        // z voxels per thread
 constexpr int kViewsPerChunk = 8;  // generic backprojection kernel
 constexpr int kViewsPerStage = 4;  // TMA backprojection kernel (two stages)
+constexpr int kMaxTapD = 128;      // largest decimation factor with a tap table
 
 struct PlanImpl {
     fdkod_geometry g{};
@@ -58,6 +59,13 @@ struct PlanImpl {
     int L = 0, log2L = 0;
     float *H = nullptr;        // ramp spectrum / L, real and even
     float2 *tw = nullptr;      // e^{-2 pi i m / L}, m < L
+    // angular low-pass of the decomposition (Sec. 2.1): symmetric taps
+    // h[|i|], |i| < H D with H = tap_blocks (triangle by default, H = 1), and
+    // per block offset r the weights of the 2H running sums,
+    // tapw[r] = (w_0 .. w_{2H-1})
+    int tap_blocks = 1;
+    double htaps[2 * kMaxTapD] = {};
+    float4 *tapw = nullptr;
     // decomposed data S'[q][j][v][t]
     float *Sp = nullptr;
     int Tstride = 0;
@@ -91,6 +99,16 @@ cudaError_t ensure_smem(size_t bytes) {
 
 // host: backprojection staging windows of a square set (cs = cos/sin per view)
 void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs);
+
+// host: angular low-pass taps h[|i|] (Sec. 2.1 leaves the kernel open):
+// the triangle (D - |i|) / D^2, |i| < D, and a Hann-windowed sinc with its
+// cutoff at the decimated Nyquist frequency, half-width H D, unit DC gain
+void triangle_taps(int D, double *h);
+void sinc_taps(int D, int H, double *h);
+// host: running-sum weights per block offset r for taps of half-width H D:
+// view j D + r adds w[r][m] = h[|r + (H - 1 - m) D|] (0 past the support) of
+// its sample to decimated view j - H + 1 + m, m < 2H (H <= 2)
+void tap_table(const double *h, int H, int D, float4 *w);
 
 // Part of the volume and detector a launch works on: detector rows
 // row0 .. row0 + nrows - 1 are the rows held by the source arrays (Q, the

@@ -28,6 +28,8 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
 double2 g_cs_host[kMaxViews];  // staging for the cos/sin upload (under g_mutex)
+double g_taps_host[fdkod::kMaxTapD];  // triangle taps and their running-sum weights (under g_mutex)
+float4 g_tapw_host[fdkod::kMaxTapD];
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -77,7 +79,7 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
     if (!g || !Q || !vol) return FDKOD_ERR_INVALID_ARG;
     if (!(g->R > 0.0) || g->N <= 0 || g->Nu <= 0 || g->Nv <= 0 || g->P <= 0 || D <= 0) return FDKOD_ERR_INVALID_ARG;
     if (g->N > (1 << 15) || g->Nu > (1 << 15) || g->Nv > (1 << 15) || g->P > kMaxViews) return FDKOD_ERR_UNSUPPORTED;
-    if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0) return FDKOD_ERR_UNSUPPORTED;
+    if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0 || D > fdkod::kMaxTapD) return FDKOD_ERR_UNSUPPORTED;
     if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;
 
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -127,6 +129,7 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
     ss.geo = (GeomEntry *)take(sizeof(GeomEntry) * n);
     ss.w0 = (int32_t *)take(sizeof(int32_t) * ss.nsq);
     ss.T = (int32_t *)take(sizeof(int32_t) * ss.nsq);
+    p.tapw = (float4 *)take(sizeof(float4) * (size_t)D);
     p.Sp = (float *)take(sizeof(float) * (size_t)p.sp_elems);
     if (off > kScratchBytes) return FDKOD_ERR_UNSUPPORTED;
     size_windows(p, ss, g_cs_host);
@@ -136,6 +139,11 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
     // every other region is fully rewritten below before it is read
     if (cudaMemsetAsync(p.status, 0, sizeof(int), st) != cudaSuccess) return FDKOD_ERR_CUDA;
     if (cudaMemcpyAsync(p.cs, g_cs_host, sizeof(double2) * g->P, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FDKOD_ERR_CUDA;
+    // the default (triangle) angular low-pass
+    triangle_taps(D, g_taps_host);
+    tap_table(g_taps_host, 1, D, g_tapw_host);
+    if (cudaMemcpyAsync(p.tapw, g_tapw_host, sizeof(float4) * D, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FDKOD_ERR_CUDA;
     if (launch_bounds(p, ss, st) != cudaSuccess) return FDKOD_ERR_CUDA;
     if (D == 1) return launch_backproject(p, ss, true, Q, vol, st) == cudaSuccess ? FDKOD_OK : FDKOD_ERR_CUDA;

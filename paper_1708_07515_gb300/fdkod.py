@@ -70,6 +70,9 @@ def load():
                 "fdkod_get_bounds": (i, [vp, vp, vp, vp, vp, vp, vp]),
                 "fdkod_last_device_status": (i, [vp, u]),
                 "fdkod_strerror": (ctypes.c_char_p, [i]),
+                "fdkod_set_decimation_taps": (i, [vp, vp, i]),
+                "fdkod_get_decimation_taps": (i, [vp, vp, i]),
+                "fdkod_sinc_taps": (i, [i, i, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -103,6 +106,7 @@ def _dev_ptr(t, what):
 # ---- C-named functions -------------------------------------------------------
 
 FDKOD_PLAN_NO_WORKSPACE = 1
+FDKOD_PLAN_SINC_TAPS = 2
 
 
 def fdkod_plan(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: int = FDKOD_F32,
@@ -164,16 +168,52 @@ def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
     return {"lo": lo, "hi": hi, "crop": crop, "phi": phi, "w0": w0, "T": T}
 
 
+def fdkod_sinc_taps(D: int, H: int = 2) -> np.ndarray:
+    """The library's Hann-windowed sinc taps h[|i|], |i| < H D (host only)."""
+    h = np.empty(max(1, H * D), np.float64)
+    _check(load().fdkod_sinc_taps(int(D), int(H), ctypes.c_void_p(h.ctypes.data)), "fdkod_sinc_taps")
+    return h
+
+
+def fdkod_set_decimation_taps(plan: int, taps) -> None:
+    h = np.ascontiguousarray(taps, dtype=np.float64).reshape(-1)
+    _check(load().fdkod_set_decimation_taps(plan, ctypes.c_void_p(h.ctypes.data), h.size),
+           "fdkod_set_decimation_taps")
+
+
+def fdkod_get_decimation_taps(plan: int) -> np.ndarray:
+    n = load().fdkod_get_decimation_taps(plan, None, 0)
+    _check(min(n, 0), "fdkod_get_decimation_taps")
+    h = np.empty(n, np.float64)
+    load().fdkod_get_decimation_taps(plan, ctypes.c_void_p(h.ctypes.data), n)
+    return h
+
+
 # ---- convenience wrapper --------------------------------------------------
 
 class Plan:
     """A plan for one geometry, decomposition level s and decimation D."""
 
     def __init__(self, R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: str = "f32",
-                 workspace: bool = True):
+                 workspace: bool = True, taps="triangle"):
+        """taps: the angular low-pass of the decomposition -- "triangle"
+        (default), "sinc" (Hann-windowed sinc, half-width 2D) or an array
+        h[|i|] of D or 2D values."""
         self.R, self.N, self.Nu, self.Nv, self.P, self.s, self.D = float(R), N, Nu, Nv, P, s, D
         self.qtype = qtype
-        self.handle = fdkod_plan(R, N, Nu, Nv, P, s, D, _DTYPES[qtype], 0 if workspace else FDKOD_PLAN_NO_WORKSPACE)
+        flags = 0 if workspace else FDKOD_PLAN_NO_WORKSPACE
+        if isinstance(taps, str):
+            if taps not in ("triangle", "sinc"):
+                raise ValueError(f"unknown taps {taps!r}")
+            if taps == "sinc":
+                flags |= FDKOD_PLAN_SINC_TAPS
+        self.handle = fdkod_plan(R, N, Nu, Nv, P, s, D, _DTYPES[qtype], flags)
+        if not isinstance(taps, str):
+            try:
+                fdkod_set_decimation_taps(self.handle, taps)
+            except Exception:
+                self.close()
+                raise
         info = PlanInfo()
         _check(load().fdkod_get_info(self.handle, ctypes.byref(info)), "fdkod_get_info")
         self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
@@ -267,6 +307,11 @@ class Plan:
                                              int(z0), int(nz), _dev_ptr(vol, "vol_slab"), _stream(Q_rows, stream)),
                "fdkod_backproject_slab")
         return vol
+
+    @property
+    def taps(self) -> np.ndarray:
+        """The angular low-pass taps h[|i|] in use."""
+        return fdkod_get_decimation_taps(self.handle)
 
     def bounds(self) -> dict:
         return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)

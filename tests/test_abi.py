@@ -47,7 +47,12 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
         assert lib.fdkod_plan(ctypes.byref(g), s, D, qt, ctypes.byref(out)) == want, (g.N, s, D, qt)
         assert out.value is None
     g = F.Geometry(64.0, 16, 16, 16, 8)
-    assert lib.fdkod_plan_ex(ctypes.byref(g), 1, 1, 0, 2, ctypes.byref(out)) == -1   # unknown flag
+    assert lib.fdkod_plan_ex(ctypes.byref(g), 1, 1, 0, 4, ctypes.byref(out)) == -1   # unknown flag
+    g256 = F.Geometry(1024.0, 256, 256, 256, 512)
+    assert lib.fdkod_plan(ctypes.byref(g256), 1, 256, 0, ctypes.byref(out)) == -2    # D above 128
+    assert lib.fdkod_set_decimation_taps(None, None, 4) == -1
+    assert lib.fdkod_get_decimation_taps(None, None, 0) == -1
+    assert lib.fdkod_sinc_taps(0, 2, None) == -1
     assert lib.fdkod_slab_rows(None, 0, 1, None, None) == -1
     assert lib.fdkod_filter_rows(None, None, 0, 1, None, 0) == -1
     assert lib.fdkod_backproject_slab(None, None, 0, 1, None, 0, 1, None, 0) == -1
@@ -66,3 +71,14 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(F, "_lib", None)
     with pytest.raises(RuntimeError):
         F.load()
+
+
+@pytest.mark.parametrize("D,H", [(1, 1), (1, 2), (2, 2), (3, 1), (4, 2), (16, 2), (128, 2)])
+def test_library_sinc_taps_match_the_oracle(lib, oracle_mod, D, H):
+    """Host-only entry (no device work): the library's windowed sinc and the
+    oracle's, written separately from the same definition."""
+    from paper_1708_07515_gb300 import fdkod as F
+    import numpy as np
+    got = F.fdkod_sinc_taps(D, H)
+    np.testing.assert_allclose(got, oracle_mod.sinc_taps(D, H), rtol=0, atol=1e-15)
+    assert lib.fdkod_sinc_taps(D, 3, None) == -1
