@@ -313,6 +313,10 @@ class Plan:
         """The angular low-pass taps h[|i|] in use."""
         return fdkod_get_decimation_taps(self.handle)
 
+    def set_taps(self, taps) -> None:
+        """Replace the angular low-pass taps (D or 2D values h[|i|])."""
+        fdkod_set_decimation_taps(self.handle, taps)
+
     def bounds(self) -> dict:
         return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)
 

@@ -1,0 +1,54 @@
+"""Learned angular taps (a linear FIR fitted to full FDK): the constrained
+least-squares solve on the host, and on the GPU the property the fit
+guarantees -- on its training scans no taps of the same support (the
+triangle and the windowed sinc among them) come closer to full FDK."""
+import numpy as np
+import pytest
+
+import phantom
+from paper_1708_07515_gb300 import learn
+
+
+def test_constrained_solve_recovers_known_taps():
+    rng = np.random.default_rng(5)
+    n = 8
+    B = rng.standard_normal((n, 500))
+    h = rng.uniform(0, 1, n)
+    h /= learn.constraint(n) @ h
+    f = h @ B
+    got = learn.solve_taps(B @ B.T, B @ f)
+    np.testing.assert_allclose(got, h, rtol=0, atol=1e-10)
+
+
+def test_constrained_solve_keeps_unit_gain():
+    rng = np.random.default_rng(6)
+    n = 6
+    B = rng.standard_normal((n, 300))
+    f = rng.standard_normal(300)          # not in the span: a true compromise
+    h = learn.solve_taps(B @ B.T, B @ f)
+    assert abs(learn.constraint(n) @ h - 1.0) < 1e-12
+    # no other unit-gain taps fit better
+    for _ in range(20):
+        d = rng.standard_normal(n)
+        d -= (learn.constraint(n) @ d) / (learn.constraint(n) @ learn.constraint(n)) * learn.constraint(n)
+        assert np.sum(((h + 1e-3 * d) @ B - f) ** 2) >= np.sum((h @ B - f) ** 2) - 1e-9
+
+
+@pytest.mark.gpu
+def test_learned_taps_are_best_on_their_training_scans():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1708_07515_gb300 as fd
+    N, P, s, D, H = 64, 96, 2, 4, 2
+    R = 4.0 * N
+    zs = [16, 32, 48]
+    projs = [torch.from_numpy(phantom.project(phantom.make_phantom(8100 + i, N, 10), R, N, N, P)).cuda()
+             for i in range(3)]
+    h = learn.learn(R, N, P, s, D, H, projs, zs)
+    tri = np.concatenate([(D - np.arange(D)) / float(D * D), np.zeros(D)])
+    errs = learn.held_out_errors(R, N, P, s, D, {"triangle": tri, "sinc": fd.fdkod_sinc_taps(D, 2), "learned": h},
+                                 projs, zs)
+    assert errs["learned"] <= errs["triangle"] * (1 + 1e-6)
+    assert errs["learned"] <= errs["sinc"] * (1 + 1e-6)
+    assert abs(learn.constraint(H * D) @ h - 1.0) < 1e-9
