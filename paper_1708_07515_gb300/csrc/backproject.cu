@@ -209,8 +209,89 @@ bp_generic_kernel(BpParams a) {
     }
 }
 
+// Unstaged form for windows too large to stage in shared memory (a source
+// close to the volume magnifies a tile's footprint on the detector): the
+// same tiling and arithmetic as bp_generic_kernel, every sample read from the
+// source in global memory (zero outside it).  Row coordinates stay relative
+// to an integer base row per view, as in the staged kernels.
+template <typename TS, bool DIRECT>
+__global__ void __launch_bounds__(kThreads)
+bp_global_kernel(BpParams a) {
+    const int tiles = a.tps * a.tps;
+    const int q = blockIdx.x / tiles;
+    const int tt = blockIdx.x - q * tiles;
+    const int qy = q / a.m, qx = q - qy * a.m;
+    int ix0, ix1, iy0, iy1;
+    square_range(qx, a.m, a.N, ix0, ix1);
+    square_range(qy, a.m, a.N, iy0, iy1);
+    const int x0 = ix0 + (tt % a.tps) * kTile;
+    const int y0 = iy0 + (tt / a.tps) * kTile;
+    if (x0 > ix1 || y0 > iy1) return;
+    const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
+    const int z0 = a.zoff + blockIdx.y * kZT;
+    const int z1 = min(z0 + kZT - 1, a.zoff + a.nz - 1);
+    const float half_n = 0.5f * (float)(a.N - 1);
+    const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;
+    const float yc = 0.5f * ((float)iy0 + (float)iy1) - half_n;
+    const float zc = 0.5f * ((float)z0 + (float)z1) - half_n;
+    const double vcd = 0.5 * (double)(a.Nv - 1);
+    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x > xe || y > ye) return;  // no block barrier below
+    const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
+    const float dz0 = (float)z0 - half_n - zc;
+    const int32_t w0q = a.w0[q];
+    const TS *src = (const TS *)a.src;
+    auto at = [&](long long off, int r, int c) -> float {  // sample (row r of the detector, column c of the source)
+        const int rr = r - a.row0;
+        return (rr >= 0 && rr < a.src_rows && c >= 0 && c < a.src_cols) ? ld_s(src + off + (long long)rr * a.row_stride + c)
+                                                                         : 0.f;
+    };
+    float acc[kZT];
+#pragma unroll
+    for (int i = 0; i < kZT; ++i) acc[i] = 0.f;
+    for (int j = 0; j < a.nviews; ++j) {
+        const int k = j * a.vstep;
+        const size_t o = (size_t)q * a.P + k;
+        const GeomEntry ge = a.geo[o];
+        const float toff = DIRECT ? ge.frac - (float)w0q : -(float)w0q;
+        const float dd = fmaf(ge.cb, dx, ge.sb * dy);
+        const float invU = ge.g_hi / fmaf(ge.r, dd, 1.0f);
+        const float t = fmaf(invU, fmaf(ge.alpha, dx, ge.gamma * dy), toff);
+        const float tf = floorf(t);
+        const float ft = t - tf;
+        const int col = (DIRECT ? a.crop[o] : 0) + (int)tf;
+        const long long off = DIRECT ? (long long)k * a.view_stride : (long long)q * a.sq_stride + (long long)j * a.view_stride;
+        const float wgt = invU * invU;
+        const double vcen = fma((double)zc, (double)ge.g_hi + (double)ge.g_lo, vcd);
+        const int vbase = (int)floor(vcen);
+        const float zq = zc * ge.r * dd;
+        const float vb = fmaf(-invU, zq, (float)(vcen - (double)vbase));
+#pragma unroll
+        for (int i = 0; i < kZT; ++i) {
+            const float v = fmaf(invU, dz0 + (float)i, vb);
+            const float vf = floorf(v);
+            const float fv = v - vf;
+            const int r = vbase + (int)vf;
+            const float s00 = at(off, r, col), s01 = at(off, r, col + 1);
+            const float s10 = at(off, r + 1, col), s11 = at(off, r + 1, col + 1);
+            const float c0 = fmaf(ft, s01 - s00, s00);
+            const float c1 = fmaf(ft, s11 - s10, s10);
+            acc[i] = fmaf(wgt, fmaf(fv, c1 - c0, c0), acc[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kZT; ++i)
+        if (z0 + i <= z1) a.vol[((size_t)(z0 + i - a.zoff) * a.N + y) * a.N + x] = acc[i] * a.scale;
+}
+
 template <typename TS, bool DIRECT>
 cudaError_t launch_t(BpParams prm, int nsq, cudaStream_t st) {
+    if (prm.J < 1) {  // one view's window does not fit shared memory: sample from global memory
+        dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.nz + kZT - 1) / kZT));
+        bp_global_kernel<TS, DIRECT><<<grid, kThreads, 0, st>>>(prm);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(float) * (size_t)prm.J * prm.Rw * (prm.Wd + 1);
     cudaError_t e = ensure_smem<bp_generic_kernel<TS, DIRECT>>(smem);
     if (e != cudaSuccess) return e;
@@ -567,8 +648,7 @@ cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool dire
     a.Wd = ss.Wd;
     a.Rw = ss.Rw;
     const size_t per_view = sizeof(float) * (size_t)ss.Rw * (ss.Wd + 1);
-    a.J = (int)std::min<size_t>(kViewsPerChunk, (200u * 1024u) / per_view);
-    if (a.J < 1) return cudaErrorInvalidConfiguration;
+    a.J = (int)std::min<size_t>(kViewsPerChunk, (200u * 1024u) / per_view);  // 0: the unstaged kernel
     a.row0 = b.row0;
     a.zoff = b.zoff;
     a.nz = b.nz;

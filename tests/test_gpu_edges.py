@@ -1,0 +1,96 @@
+"""Edge cases of the GPU path against the FP64 oracle: the smallest volumes
+(one voxel, squares of one voxel), the widest detector the filter takes
+(Nu = 2048), a source just outside the volume's circumscribed cylinder and
+a nearly parallel beam, one view, and plans that must be rejected.  Bars as
+in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import phantom
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_RMSE = 1e-5
+MAX_REL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def fd():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1708_07515_gb300 as fd
+    fd.load()
+    return fd
+
+
+def _cmp(got, want, what):
+    err = got.astype(np.float64) - want
+    rel = np.linalg.norm(err) / np.linalg.norm(want)
+    mx = np.abs(err).max() / np.abs(want).max()
+    assert rel <= REL_RMSE and mx <= MAX_REL, f"{what}: rel-RMSE {rel:.3e}, max-rel {mx:.3e}"
+
+
+@pytest.mark.parametrize("N,P,s,D,Nu,Nv", [
+    (1, 8, 0, 2, 4, 4),      # one voxel
+    (2, 8, 1, 2, 4, 4),      # squares of one voxel
+    (3, 12, 1, 3, 5, 3),     # ragged squares (1 and 2 voxels), odd detector
+    (5, 1, 1, 1, 8, 8),      # one view
+])
+def test_tiny_volumes(fd, oracle_mod, N, P, s, D, Nu, Nv):
+    R = 4.0 * N + 2.0
+    Q = np.random.default_rng(800 + N).standard_normal((P, Nv, Nu)).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    with fd.Plan(R, N, Nu, Nv, P, s, D) as plan:
+        od = plan.backproject(Qd).cpu().numpy()
+        pl = plan.backproject_plain(Qd).cpu().numpy()
+        assert plan.device_status() == 0
+    _cmp(od, oracle_mod.fdkod(Q, R, N, s, D), f"FDK-OD N={N}")
+    _cmp(pl, oracle_mod.fdk(Q, R, N), f"plain FDK N={N}")
+
+
+@pytest.mark.parametrize("R", [None, 1000.0 * 32])
+def test_extreme_source_distances(fd, oracle_mod, R):
+    """R just above the limit sqrt(2) N / 2 + 1 (magnification ~20: one
+    view's window outgrows shared memory, so the unstaged kernel runs) and a
+    nearly parallel beam."""
+    N, P, s, D = 32, 48, 2, 4
+    R = np.sqrt(2.0) * N / 2 + 1.2 if R is None else R
+    p = phantom.project(phantom.make_phantom(810, N, 6), R, N, N, P)
+    Q = oracle_mod.filter(p, R).astype(np.float32)
+    Qd = torch.from_numpy(Q).cuda()
+    with fd.Plan(R, N, N, N, P, s, D) as plan:
+        od = plan.backproject(Qd).cpu().numpy()
+        pl = plan.backproject_plain(Qd).cpu().numpy()
+        assert plan.device_status() == 0
+    _cmp(od, oracle_mod.fdkod(Q, R, N, s, D), f"FDK-OD R={R:.1f}")
+    _cmp(pl, oracle_mod.fdk(Q, R, N), f"plain FDK R={R:.1f}")
+
+
+def test_widest_detector_filter(fd, oracle_mod):
+    """Nu = 2048 (L = 4096, 256 threads per row pair)."""
+    N, Nu, Nv, P = 64, 2048, 6, 3
+    R = 4.0 * N
+    proj = np.random.default_rng(820).uniform(0.0, 1.0, (P, Nv, Nu)).astype(np.float32)
+    with fd.Plan(R, N, Nu, Nv, P, 0, 1) as plan:
+        Q = plan.filter(torch.from_numpy(proj).cuda()).cpu().numpy()
+    want = oracle_mod.filter(proj, R)
+    # FFT round-off bar of test_gpu_parity.py: 2 log2(L) 2^-24 times the norm
+    # of the cosine-weighted row pair sharing one transform
+    L = 4096
+    a = np.arange(Nu) - (Nu - 1) / 2
+    b = np.arange(Nv) - (Nv - 1) / 2
+    q = proj.astype(np.float64) * (R / np.sqrt(R * R + a[None, :] ** 2 + b[:, None] ** 2))[None]
+    rn = np.linalg.norm(q, axis=-1).reshape(-1)
+    pair = np.repeat(np.sqrt(np.add.reduceat(rn ** 2, np.arange(0, rn.size, 2))), 2)[:rn.size]
+    err = np.abs(Q.astype(np.float64) - want).max(axis=-1).reshape(-1)
+    assert np.all(err <= 2 * np.log2(L) * 2.0 ** -24 * pair)
+
+
+def test_rejected_plans(fd):
+    for args in [(10.0, 16, 16, 16, 8, 1, 1),     # source inside the volume
+                 (64.0, 16, 4096, 16, 8, 1, 1),   # detector wider than the filter takes
+                 (64.0, 16, 16, 16, 8, 1, 3)]:    # D does not divide P
+        with pytest.raises(fd.FdkodError) as e:
+            fd.Plan(*args)
+        assert e.value.status == -2
