@@ -91,22 +91,30 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
 // TMA path: one CTA per (square q, band of VB detector rows), warp
 // specialised.  The producer warp's lane 0 brings each view's crop box
 // (VB rows x Wc columns starting at the 16-byte aligned column below
-// crop[q][k]) into a ring of kStages slots of kG views with 3D bulk-tensor
-// copies (zero fill outside the detector); slot n is full when its bytes
-// have landed (mbarrier full[n]) and free again when all consumer warps
-// have arrived on empty[n].  No block-wide barrier inside the view loop.
+// crop[q][k]) into a ring of kStages slots of kG views (Ring<TQ>) with 3D
+// bulk-tensor copies (zero fill outside the detector); slot n is full when
+// its bytes have landed (mbarrier full[n]) and free again when all consumer
+// warps have arrived on empty[n].  No block-wide barrier inside the view loop.
 //
-// Consumers: LPR lanes share a detector row and each lane owns C
-// consecutive columns t0 .. t0 + C - 1, so one view costs the lane a few
-// vector shared loads at compile-time offsets (the column offset of the
-// crop inside its aligned box selects one of four code paths, uniform per
-// view) and, per column, one lerp and the 2H tap FMAs.  Everything else
+// Consumers: LPR lanes share a pair of adjacent detector rows and each lane
+// owns C consecutive columns t0 .. t0 + C - 1 of both (kRowsPerLane), so one
+// view costs the lane a few vector shared loads at compile-time offsets per
+// row (the column offset of the crop inside its aligned box selects one of
+// four code paths, uniform per view) and, per column, one lerp and the 2H
+// tap FMAs; the per-view bookkeeping is shared by the two rows.  Everything else
 // a view needs -- shift fraction, which tap weights apply and whether a
 // decimated view is complete -- is one 8-byte entry of a per-CTA table in
 // stream order, built once from crop[q][.] and frac[q][.], plus the weights
 // w[r] of its block offset r (one 16-byte entry per r).
 
-constexpr int kConsumerWarps = 8, kG = 4, kStages = 3;
+constexpr int kConsumerWarps = 8;
+constexpr int kRowsPerLane = 2;  // adjacent detector rows per lane: the per-view work is shared
+// ring shape per element type (measured): slots of kG views, kStages slots
+template <typename TQ>
+struct Ring {
+    static constexpr int kG = sizeof(TQ) == 4 ? 2 : 4;
+    static constexpr int kStages = 3;
+};
 constexpr int kDecThreads = 32 * (kConsumerWarps + 1);
 constexpr int kRingSlack = 128;  // bytes after the ring: vector loads of the last row may run past its end
 constexpr uint64_t kDecWaitNs = 2000000000ull;
@@ -189,22 +197,26 @@ struct VecLoad<__half, NV> {
     }
 };
 
-// One view for one lane: columns t0 + i (i < C) sample the row at box column
-// O + i (+ the shift fraction f) and feed the 2H running sums with weights w.
-template <typename TQ, int C, int O, int H>
-__device__ __forceinline__ void view_cols(uint32_t a, float f, float4 w, float (*acc)[C]) {
+// One view for one lane: in each of its RPL rows (row stride rs bytes),
+// columns t0 + i (i < C) sample the row at box column O + i (+ the shift
+// fraction f) and feed that row's 2H running sums with weights w.
+template <typename TQ, int C, int O, int H, int RPL>
+__device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, float4 w, float (*acc)[2 * H][C]) {
     constexpr int NV = (O + C) / 4 + 1;  // vectors covering elements O .. O + C
-    float e[4 * NV];
-    VecLoad<TQ, NV>::f(a, e);
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-        const float a0 = e[O + i], a1 = e[O + i + 1];
-        const float smp = fmaf(f, a1 - a0, a0);
-        acc[0][i] = fmaf(w.x, smp, acc[0][i]);
-        acc[1][i] = fmaf(w.y, smp, acc[1][i]);
-        if (H == 2) {
-            acc[2][i] = fmaf(w.z, smp, acc[2][i]);
-            acc[3][i] = fmaf(w.w, smp, acc[3][i]);
+    for (int r = 0; r < RPL; ++r) {
+        float e[4 * NV];
+        VecLoad<TQ, NV>::f(a + rs * (uint32_t)r, e);
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const float a0 = e[O + i], a1 = e[O + i + 1];
+            const float smp = fmaf(f, a1 - a0, a0);
+            acc[r][0][i] = fmaf(w.x, smp, acc[r][0][i]);
+            acc[r][1][i] = fmaf(w.y, smp, acc[r][1][i]);
+            if (H == 2) {
+                acc[r][2][i] = fmaf(w.z, smp, acc[r][2][i]);
+                acc[r][3][i] = fmaf(w.w, smp, acc[r][3][i]);
+            }
         }
     }
 }
@@ -212,14 +224,15 @@ __device__ __forceinline__ void view_cols(uint32_t a, float f, float4 w, float (
 // off: the crop's offset inside its 16-byte aligned box (elements).  For
 // 16-bit data the vectors are 8 bytes, so the lane's address moves by whole
 // vectors and the remainder (0..3) picks the code path.
-template <typename TQ, int C, int H>
-__device__ __forceinline__ void view_step(uint32_t a, int off, float f, float4 w, float (*acc)[C]) {
+template <typename TQ, int C, int H, int RPL>
+__device__ __forceinline__ void view_step(uint32_t a, uint32_t rs, int off, float f, float4 w,
+                                          float (*acc)[2 * H][C]) {
     if (sizeof(TQ) == 2) a += 8u * (uint32_t)(off >> 2);
     switch (off & 3) {
-        case 0: view_cols<TQ, C, 0, H>(a, f, w, acc); break;
-        case 1: view_cols<TQ, C, 1, H>(a, f, w, acc); break;
-        case 2: view_cols<TQ, C, 2, H>(a, f, w, acc); break;
-        default: view_cols<TQ, C, 3, H>(a, f, w, acc); break;
+        case 0: view_cols<TQ, C, 0, H, RPL>(a, rs, f, w, acc); break;
+        case 1: view_cols<TQ, C, 1, H, RPL>(a, rs, f, w, acc); break;
+        case 2: view_cols<TQ, C, 2, H, RPL>(a, rs, f, w, acc); break;
+        default: view_cols<TQ, C, 3, H, RPL>(a, rs, f, w, acc); break;
     }
 }
 
@@ -231,7 +244,9 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                      int D, int Pd, int Nv, int Wc, int tile_stride) {
     constexpr int ES = (int)sizeof(TQ);
     constexpr int kAlign = 16 / ES;
-    constexpr int RPW = 32 / LPR;              // detector rows per consumer warp
+    constexpr int kG = Ring<TQ>::kG, kStages = Ring<TQ>::kStages;
+    constexpr int RPL = kRowsPerLane;
+    constexpr int RPW = 32 / LPR * RPL;        // detector rows per consumer warp
     constexpr int VB = kConsumerWarps * RPW;   // rows per CTA (box height)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ring = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
@@ -287,20 +302,23 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
         return;
     }
 
-    const int rib = ty * RPW + tx / LPR;  // row in the band
-    const int t0 = (tx % LPR) * C;        // first column of the lane
+    const int rib = (ty * (32 / LPR) + tx / LPR) * RPL;  // first of the lane's rows in the band
+    const int t0 = (tx % LPR) * C;                      // first column of the lane
     const int v = v0 + rib;
     const int T = Tq[q];
     const bool act = t0 < T;
-    const bool store = v < Nv && t0 < Tstride;
-    float acc[2 * H][C];
+    const bool store = t0 < Tstride;
+    float acc[RPL][2 * H][C];
 #pragma unroll
-    for (int m = 0; m < 2 * H; ++m)
+    for (int r = 0; r < RPL; ++r)
 #pragma unroll
-        for (int i = 0; i < C; ++i) acc[m][i] = 0.f;
+        for (int m = 0; m < 2 * H; ++m)
+#pragma unroll
+            for (int i = 0; i < C; ++i) acc[r][m][i] = 0.f;
     const size_t vstride = (size_t)Nv * Tstride;
-    float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + t0;
+    float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + t0;  // row v; row v + r is r Tstride further
     const uint32_t lane_addr = tma::smem_u32(ring) + (uint32_t)(ES * (rib * Wc + t0));
+    const uint32_t row_bytes = (uint32_t)(ES * Wc);
     int slot = 0;
     uint32_t phase = 0;
 
@@ -318,24 +336,34 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                 const float2 fc = s_fc[n * kG + w];
                 const int code = __float_as_int(fc.y);
                 const float4 tp = s_taps[(code >> kCodeTapShift) & 255];
-                if (act) view_step<TQ, C, H>(sa + tile_bytes * (uint32_t)w, code & (kAlign - 1), fc.x, tp, acc);
+                if (act)
+                    view_step<TQ, C, H, RPL>(sa + tile_bytes * (uint32_t)w, row_bytes, code & (kAlign - 1), fc.x, tp,
+                                             acc);
                 if (code & kCodeRotate) {
                     const int jst = (code >> kCodeStoreShift) - 1;
                     if (jst >= 0 && store) {
-                        float o[C];
 #pragma unroll
-                        for (int i = 0; i < C; ++i) o[i] = t0 + i < T ? acc[0][i] : 0.f;
-                        float4 *dst = (float4 *)(out + (size_t)jst * vstride);
+                        for (int r = 0; r < RPL; ++r) {
+                            if (v + r < Nv) {
+                                float o[C];
 #pragma unroll
-                        for (int i = 0; i < C / 4; ++i)  // Tstride is a multiple of 4
-                            if (t0 + 4 * i < Tstride) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                                for (int i = 0; i < C; ++i) o[i] = t0 + i < T ? acc[r][0][i] : 0.f;
+                                float4 *dst = (float4 *)(out + (size_t)jst * vstride + (size_t)r * Tstride);
+#pragma unroll
+                                for (int i = 0; i < C / 4; ++i)  // Tstride is a multiple of 4
+                                    if (t0 + 4 * i < Tstride)
+                                        dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                            }
+                        }
                     }
 #pragma unroll
-                    for (int i = 0; i < C; ++i) {
+                    for (int r = 0; r < RPL; ++r)
 #pragma unroll
-                        for (int m = 0; m < 2 * H - 1; ++m) acc[m][i] = acc[m + 1][i];
-                        acc[2 * H - 1][i] = 0.f;
-                    }
+                        for (int i = 0; i < C; ++i) {
+#pragma unroll
+                            for (int m = 0; m < 2 * H - 1; ++m) acc[r][m][i] = acc[r][m + 1][i];
+                            acc[r][2 * H - 1][i] = 0.f;
+                        }
                 }
             }
         }
@@ -364,7 +392,7 @@ cudaError_t launch_tma_shape(const PlanImpl &p, const CUtensorMap &map, float *o
                              int nrows, size_t smem, int tile_stride) {
     cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, LPR, H>>(smem);
     if (e != cudaSuccess) return e;
-    constexpr int VB = kConsumerWarps * (32 / LPR);
+    constexpr int VB = kConsumerWarps * (32 / LPR) * kRowsPerLane;
     dim3 grid(p.od.nsq, (nrows + VB - 1) / VB);
     decompose_tma_kernel<TQ, C, LPR, H><<<grid, kDecThreads, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T,
                                                                          p.tapw, p.status, p.Tstride, p.g.P, p.D,
@@ -393,10 +421,11 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
     if (Wc > 256 || p.Tstride > 256 || p.D > kMaxTapD) return cudaSuccess;  // block offset: 8 bits of the code
     const DecShape sh = dec_shape(p.Tstride);
-    const int VB = kConsumerWarps * (32 / sh.LPR);
+    const int VB = kConsumerWarps * (32 / sh.LPR) * kRowsPerLane;
     const int tile_stride = (VB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
     const int nstream = p.g.P + (2 * p.tap_blocks - 1) * p.D - 1;
-    const size_t smem = 128 + sizeof(TQ) * (size_t)kStages * kG * tile_stride + kRingSlack + 16 * (size_t)p.D +
+    const size_t smem = 128 + sizeof(TQ) * (size_t)Ring<TQ>::kStages * Ring<TQ>::kG * tile_stride + kRingSlack +
+                        16 * (size_t)p.D +
                         12 * (size_t)nstream;
     if (smem > 200 * 1024) return cudaSuccess;
     CUtensorMap map;
