@@ -115,32 +115,49 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 // e^{-2 pi i r (j mod Ns) / (Ns R)}, does an R-point DFT and writes sample
 // r to (j - j mod Ns) R + (j mod Ns) + r Ns.  Each thread owns 16/R items
 // (16 values), all loaded before the barrier that precedes the stores.
+// L, Ns and L/R are powers of two, so j mod Ns is a mask and the twiddle
+// index a shift; when the read stride L/R (write stride Ns) is a multiple of
+// 16, the padded index of sample r is the padded index of sample 0 plus r
+// times the padded stride, one add per sample.  Ns is 1 on the first pass
+// (its samples are consecutive within one 16-block) and a multiple of 16
+// after it.
 template <int R>
-__device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int L, int Ns, int lt, int nt) {
+__device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int lgL, int lgNs, int lt, int nt) {
     constexpr int kItems = 16 / R;
-    const int n_items = L / R;
-    const int tstep = L / (Ns * R);
+    constexpr int lgR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+    const int n_items = 1 << (lgL - lgR);
+    const int Ns = 1 << lgNs;
+    const int lg_tstep = lgL - lgNs - lgR;
+    const bool whole_in = n_items >= 16;       // read stride: whole 16-blocks
+    const int pin = n_items + (n_items >> 4);  // its padded length
+    const int pout = Ns + (Ns >> 4);           // padded write stride (Ns >= 16)
     float2 v[kItems][R];
     int dst[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const int j = lt + it * nt;
-        const int k = j % Ns;
+        const int k = j & (Ns - 1);
+        if (whole_in) {
+            const int b0 = pad(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[it][r] = buf[pad(j + r * n_items)];
+            for (int r = 0; r < R; ++r) v[it][r] = buf[b0 + r * pin];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[it][r] = buf[pad(j + r * n_items)];
+        }
         if (Ns > 1) {
             float2 w[R];
-            w[1] = tw[k * tstep];
-            if (R >= 4) w[2] = tw[2 * k * tstep];
+            w[1] = tw[k << lg_tstep];
+            if (R >= 4) w[2] = tw[(2 * k) << lg_tstep];
             if (R >= 4) w[3] = cmul(w[1], w[2]);
             if (R >= 8) {
-                w[4] = tw[4 * k * tstep];
+                w[4] = tw[(4 * k) << lg_tstep];
                 w[5] = cmul(w[1], w[4]);
                 w[6] = cmul(w[2], w[4]);
                 w[7] = cmul(w[3], w[4]);
             }
             if (R >= 16) {
-                w[8] = tw[8 * k * tstep];
+                w[8] = tw[(8 * k) << lg_tstep];
 #pragma unroll
                 for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
             }
@@ -148,35 +165,36 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw,
             for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
         }
         dft<R>(v[it]);
-        dst[it] = (j - k) * R + k;
+        dst[it] = pad(((j - k) << lgR) + k);
     }
     __syncthreads();
+    const int sstride = Ns == 1 ? 1 : pout;  // Ns = 1: R <= 16 consecutive samples of one 16-block
 #pragma unroll
     for (int it = 0; it < kItems; ++it)
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad(dst[it] + r * Ns)] = v[it][out_pos<R>(r)];
+        for (int r = 0; r < R; ++r) buf[dst[it] + r * sstride] = v[it][out_pos<R>(r)];
     __syncthreads();
 }
 
 // Forward DFT of length L = 2^log2L (>= 16) in place: radix-16 passes, then
 // one pass of radix 2, 4 or 8 for the remaining factor.
-__device__ __forceinline__ void fft_forward(float2 *buf, const float2 *tw, int L, int lt, int nt) {
-    int Ns = 1;
-    while (Ns * 16 <= L) {
-        pass<16>(buf, tw, L, Ns, lt, nt);
-        Ns *= 16;
+__device__ __forceinline__ void fft_forward(float2 *buf, const float2 *tw, int lgL, int lt, int nt) {
+    int lgNs = 0;
+    while (lgNs + 4 <= lgL) {
+        pass<16>(buf, tw, lgL, lgNs, lt, nt);
+        lgNs += 4;
     }
-    const int rest = L / Ns;
-    if (rest == 8) pass<8>(buf, tw, L, Ns, lt, nt);
-    else if (rest == 4) pass<4>(buf, tw, L, Ns, lt, nt);
-    else if (rest == 2) pass<2>(buf, tw, L, Ns, lt, nt);
+    const int rest = lgL - lgNs;
+    if (rest == 3) pass<8>(buf, tw, lgL, lgNs, lt, nt);
+    else if (rest == 2) pass<4>(buf, tw, lgL, lgNs, lt, nt);
+    else if (rest == 1) pass<2>(buf, tw, lgL, lgNs, lt, nt);
 }
 
 // G row pairs per CTA, L/16 threads per pair.
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
-              const float2 *__restrict__ tw, int L, int G, int Nu, int Nv, int row0, int rows_per_view,
+              const float2 *__restrict__ tw, int L, int lgL, int G, int Nu, int Nv, int row0, int rows_per_view,
               long long nrows, float R) {
     extern __shared__ float2 z[];
     const int nt = L / 16;
@@ -199,7 +217,7 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
         buf[pad(i)] = v;
     }
     __syncthreads();
-    fft_forward(buf, tw, L, lt, nt);
+    fft_forward(buf, tw, lgL, lt, nt);
     // product with the real, even ramp spectrum (1/L folded in), conjugated:
     // the inverse transform is the conjugate of a forward transform
     for (int i = lt; i < L; i += nt) {
@@ -208,7 +226,7 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
         buf[pad(i)] = make_float2(v.x * h, -v.y * h);
     }
     __syncthreads();
-    fft_forward(buf, tw, L, lt, nt);
+    fft_forward(buf, tw, lgL, lt, nt);
     for (int u = lt; u < Nu; u += nt) {
         const float2 v = buf[pad(u)];
         if (hasA) Q[rowA * Nu + u] = to_q<TQ>(v.x);
@@ -225,7 +243,7 @@ cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t s
     const size_t smem = sizeof(float2) * (size_t)G * (p.L + p.L / 16);
     cudaError_t e = ensure_smem<filter_kernel<TQ>>(smem);
     if (e != cudaSuccess) return e;
-    filter_kernel<TQ><<<(unsigned)blocks, G * (p.L / 16), smem, st>>>(proj, Q, p.H, p.tw, p.L, G, p.g.Nu, p.g.Nv,
+    filter_kernel<TQ><<<(unsigned)blocks, G * (p.L / 16), smem, st>>>(proj, Q, p.H, p.tw, p.L, p.log2L, G, p.g.Nu, p.g.Nv,
                                                                       row0, rows_per_view, nrows, (float)p.g.R);
     return cudaGetLastError();
 }
