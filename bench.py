@@ -60,8 +60,9 @@ def parse():
                     help="64 volumes of uneven size (N in {64..384}, P = 1.4 N) in one CUDA graph")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the filtered projections (arithmetic stays float32)")
-    ap.add_argument("--taps", choices=["triangle", "sinc"], default="triangle",
-                    help="angular low-pass of the decomposition (Sec. 2.1): triangle or Hann-windowed sinc")
+    ap.add_argument("--taps", choices=["triangle", "sinc", "learned"], default="triangle",
+                    help="angular low-pass of the decomposition (Sec. 2.1): triangle, Hann-windowed sinc, or taps "
+                         "fitted to full FDK on separate training scans before the run (learn.py)")
     return ap.parse_args()
 
 
@@ -94,6 +95,18 @@ def oracle_sample(w, proj, zs, oracle):
     Q = np.zeros((w.P, w.Nv, w.Nu), dtype=np.float64)
     Q.reshape(-1, w.Nu)[flat] = Qr
     oracle.fdkod_slices(Q, w.R, w.N, w.s, w.D, zs)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_fdk(w, proj, zs, oracle):
+    """The same bounded sample through the oracle's plain FDK.  Returns seconds."""
+    rows = rows_for_slices(w.N, w.Nv, w.R, zs)
+    flat = np.array([k * w.Nv + v for k in range(w.P) for v in rows], dtype=np.int64)
+    t0 = time.perf_counter()
+    Qr = oracle.filter_rows(proj, w.R, flat)
+    Q = np.zeros((w.P, w.Nv, w.Nu), dtype=np.float64)
+    Q.reshape(-1, w.Nu)[flat] = Qr
+    oracle.fdk_slices(Q, w.R, w.N, zs)
     return time.perf_counter() - t0
 
 
@@ -293,7 +306,16 @@ def main():
         if w.noise:
             phantom.add_noise(proj, w.noise, w.seed + rank)
 
-    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=args.taps)
+    taps = args.taps
+    if taps == "learned":
+        # 2D taps fitted on 4 noise-free training scans (other seeds), 16 slices each
+        from paper_1708_07515_gb300 import learn
+        train = [phantom.project_gpu(phantom.make_phantom(8000 + i, w.N, w.n_ell), w.R, w.Nu, w.Nv, w.P)
+                 for i in range(4)]
+        zs_fit = np.linspace(w.N // 8, w.N - 1 - w.N // 8, 16).round().astype(int)
+        taps = learn.learn(w.R, w.N, w.P, w.s, w.D, 2, train, zs_fit)
+        del train
+    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=taps)
     info = plan.info
     stream = torch.cuda.current_stream()
     proj_d = torch.from_numpy(proj).cuda()
@@ -428,7 +450,7 @@ def main():
         Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
         ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
         ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
-                                     taps=oracle.sinc_taps(w.D) if args.taps == "sinc" else None)
+                                     taps=None if args.taps == "triangle" else plan.taps)
         g = vol_od[zs].astype(np.float64)
         extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(g - ref_od) / np.linalg.norm(ref_od))
         extra["rel_rmse_vs_fp64_fdk_oracle"] = float(np.linalg.norm(g - ref_fdk) / np.linalg.norm(ref_fdk))
@@ -445,6 +467,10 @@ def main():
                    "kind": "oracle",
                    "sample": f"{len(done)} seeded slices of {w.name}, each: FP64 direct-convolution filter of "
                              f"the rows it needs + FP64 FDK-OD of the slice ({t:.1f} s total)"}
+            # the oracle's plain FDK on the first of those slices, for the CPU-side speedup
+            tf = oracle_sample_fdk(w, proj, done[:1], oracle)
+            cpu["plain_fdk_value"] = w.N * w.N * w.P / tf
+            cpu["plain_fdk_sample"] = f"slice {done[0]}: FP64 filter of its rows + FP64 plain FDK ({tf:.1f} s)"
 
     clocks = clk.summary()
     peaks = measured_peaks()
@@ -489,6 +515,9 @@ def main():
             "plain_fdk": {"value": world * upd_eff / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "step": "filter + plain backprojection"},
             "speedup_vs_plain_fdk": ms_plain / ms_step,
+            "actual_updates_per_s": {"step": world * float(w.N) ** 3 * (w.P // w.D) / (ms_step * 1e-3),
+                                     "backprojection": upd_bp / (bp_ms * 1e-3),
+                                     "note": "N^3 P / D updates (the work FDK-OD does) per second"},
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

@@ -97,7 +97,7 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
 // warps have arrived on empty[n].  No block-wide barrier inside the view loop.
 //
 // Consumers: LPR lanes share a pair of adjacent detector rows and each lane
-// owns C consecutive columns t0 .. t0 + C - 1 of both (kRowsPerLane), so one
+// owns C consecutive columns t0 .. t0 + C - 1 of both (rows_per_lane), so one
 // view costs the lane a few vector shared loads at compile-time offsets per
 // row (the column offset of the crop inside its aligned box selects one of
 // four code paths, uniform per view) and, per column, one lerp and the 2H
@@ -108,7 +108,10 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
 // w[r] of its block offset r (one 16-byte entry per r).
 
 constexpr int kConsumerWarps = 8;
-constexpr int kRowsPerLane = 2;  // adjacent detector rows per lane: the per-view work is shared
+// adjacent detector rows per lane (the per-view work is shared): two with
+// the triangle's two running sums, one with the four of 2D-tap filters
+// (registers; measured)
+__host__ __device__ constexpr int rows_per_lane(int H) { return H == 1 ? 2 : 1; }
 // ring shape per element type (measured): slots of kG views, kStages slots
 template <typename TQ>
 struct Ring {
@@ -245,7 +248,7 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     constexpr int ES = (int)sizeof(TQ);
     constexpr int kAlign = 16 / ES;
     constexpr int kG = Ring<TQ>::kG, kStages = Ring<TQ>::kStages;
-    constexpr int RPL = kRowsPerLane;
+    constexpr int RPL = rows_per_lane(H);
     constexpr int RPW = 32 / LPR * RPL;        // detector rows per consumer warp
     constexpr int VB = kConsumerWarps * RPW;   // rows per CTA (box height)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -392,7 +395,7 @@ cudaError_t launch_tma_shape(const PlanImpl &p, const CUtensorMap &map, float *o
                              int nrows, size_t smem, int tile_stride) {
     cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, LPR, H>>(smem);
     if (e != cudaSuccess) return e;
-    constexpr int VB = kConsumerWarps * (32 / LPR) * kRowsPerLane;
+    constexpr int VB = kConsumerWarps * (32 / LPR) * rows_per_lane(H);
     dim3 grid(p.od.nsq, (nrows + VB - 1) / VB);
     decompose_tma_kernel<TQ, C, LPR, H><<<grid, kDecThreads, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T,
                                                                          p.tapw, p.status, p.Tstride, p.g.P, p.D,
@@ -421,7 +424,7 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
     if (Wc > 256 || p.Tstride > 256 || p.D > kMaxTapD) return cudaSuccess;  // block offset: 8 bits of the code
     const DecShape sh = dec_shape(p.Tstride);
-    const int VB = kConsumerWarps * (32 / sh.LPR) * kRowsPerLane;
+    const int VB = kConsumerWarps * (32 / sh.LPR) * rows_per_lane(p.tap_blocks);
     const int tile_stride = (VB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
     const int nstream = p.g.P + (2 * p.tap_blocks - 1) * p.D - 1;
     const size_t smem = 128 + sizeof(TQ) * (size_t)Ring<TQ>::kStages * Ring<TQ>::kG * tile_stride + kRingSlack +
