@@ -1,8 +1,9 @@
 """Edge cases of the GPU path against the FP64 oracle: the smallest volumes
 (one voxel, squares of one voxel), the widest detector the filter takes
 (Nu = 2048), a source just outside the volume's circumscribed cylinder and
-a nearly parallel beam, one view, and plans that must be rejected.  Bars as
-in test_gpu_parity.py."""
+a nearly parallel beam, one view; plans that must be rejected or that run
+out of device memory; two plans working concurrently.  Bars as in
+test_gpu_parity.py."""
 import numpy as np
 import pytest
 
@@ -94,3 +95,44 @@ def test_rejected_plans(fd):
         with pytest.raises(fd.FdkodError) as e:
             fd.Plan(*args)
         assert e.value.status == -2
+
+
+def test_out_of_memory_plan_fails_cleanly(fd):
+    """A plan whose decomposed-data workspace cannot exist (s = 0, 32768
+    detector rows, ~10^14 bytes) returns FDKOD_ERR_OOM, frees what it had
+    allocated, and the library keeps working."""
+    with pytest.raises(fd.FdkodError) as e:
+        fd.Plan(4.0 * 2048, 2048, 2048, 32768, 2048, 0, 2)
+    assert e.value.status == -4
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        with pytest.raises(fd.FdkodError):
+            fd.Plan(4.0 * 2048, 2048, 2048, 32768, 2048, 0, 2)
+    free1, _ = torch.cuda.mem_get_info()
+    assert abs(free1 - free0) < 64 << 20          # nothing left behind
+    N, P = 32, 48
+    Q = torch.from_numpy(np.random.default_rng(830).standard_normal((P, N, N)).astype(np.float32)).cuda()
+    with fd.Plan(4.0 * N, N, N, N, P, 2, 4) as plan:
+        plan.backproject(Q)
+        assert plan.device_status() == 0
+
+
+def test_concurrent_plans_on_two_streams(fd):
+    """Two plans (different geometries) enqueued on two streams at once give
+    the same volumes as one after the other."""
+    rng = np.random.default_rng(840)
+    Qa = torch.from_numpy(rng.standard_normal((96, 64, 64)).astype(np.float32)).cuda()
+    Qb = torch.from_numpy(rng.standard_normal((60, 50, 53)).astype(np.float32)).cuda()
+    with fd.Plan(256.0, 64, 64, 64, 96, 3, 4) as pa, fd.Plan(200.0, 50, 53, 50, 60, 2, 3) as pb:
+        ref_a = pa.backproject(Qa).clone()
+        ref_b = pb.backproject(Qb).clone()
+        torch.cuda.synchronize()
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        va = torch.empty_like(ref_a)
+        vb = torch.empty_like(ref_b)
+        for _ in range(3):
+            pa.backproject(Qa, va, sa.cuda_stream)
+            pb.backproject(Qb, vb, sb.cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(va, ref_a) and torch.equal(vb, ref_b)
+        assert pa.device_status() == 0 and pb.device_status() == 0
