@@ -272,6 +272,30 @@ int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, const float
                               uintptr_t stream);
 
 /*
+ * Whole slab-wise reconstruction from host buffers (piecemeal FDK-OD,
+ * Sec. 2.2): the device holds two bands of detector rows and two slabs at a
+ * time, never the whole projection set or volume.  Per slab of `slab`
+ * slices: one strided copy uploads, from every view, the detector rows the
+ * slab needs (fdkod_slab_rows); the filter, decomposition and backprojection
+ * run on `stream`; the slab is copied back.  Uploads and read-backs run on
+ * streams of their own, double-buffered, so they overlap the neighbouring
+ * slabs' compute.
+ *
+ * proj_host: host [P][Nv][Nu] float32 (page-locked memory lets the copies
+ *   overlap the compute; pageable memory works, with synchronous copies);
+ * vol_host: host [N][N][N] float32, fully overwritten;
+ * slab: slices per slab (>= 1, clamped to N);
+ * device_bytes: if not NULL, receives the device memory the call allocated
+ *   (all of it is freed before the call returns).
+ * Works with plans with or without the whole-volume workspace; the plan's
+ * decimation taps and storage type apply.  Synchronous: returns once
+ * vol_host holds the volume and the device status word has been read.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT, BOUNDS.
+ */
+int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_host, float *vol_host, int slab,
+                            uintptr_t stream, int64_t *device_bytes);
+
+/*
  * Angular low-pass of the decomposition (Sec. 2.1: low-pass filter over the
  * angles, then keep every D-th).  The filter is symmetric and circular over
  * the orbit: decimated view j is sum_i h[|i|] S[(jD + i) mod P], |i| < n,

@@ -73,6 +73,7 @@ def load():
                 "fdkod_set_decimation_taps": (i, [vp, vp, i]),
                 "fdkod_get_decimation_taps": (i, [vp, vp, i]),
                 "fdkod_sinc_taps": (i, [i, i, vp]),
+                "fdkod_reconstruct_slabs": (i, [vp, vp, vp, i, u, ctypes.POINTER(ctypes.c_int64)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -326,25 +327,38 @@ class Plan:
         return int(load().fdkod_last_device_status(self.handle, st))
 
 
-def reconstruct_slabs(plan: Plan, proj_host, slab: int, out=None):
-    """Piecemeal FDK-OD (Sec. 2.2): for each slab of `slab` slices, upload only
-    the detector rows it needs, filter them, decompose and backproject the
-    slab, and copy it back.  proj_host: numpy float32 [P][Nv][Nu]; returns a
-    numpy float32 [N][N][N] (or fills `out`).  Device memory holds one band
-    of projections, its filtered rows, its decomposed data and one slab."""
+def reconstruct_slabs(plan: Plan, proj_host, slab: int, out=None, stream=None):
+    """Piecemeal FDK-OD (Sec. 2.2) through fdkod_reconstruct_slabs: the
+    library uploads, for each slab of `slab` slices, only the detector rows it
+    needs, filters, decomposes and backprojects them and copies the slab
+    back, pipelined over three streams.  proj_host: float32 [P][Nv][Nu] host
+    array (numpy, or a torch CPU tensor -- page-locked memory lets the copies
+    overlap the compute); returns the float32 [N][N][N] volume (numpy, or
+    `out`, numpy or torch CPU).  plan.last_slab_device_bytes records the
+    device memory the call used."""
     import numpy as np
-    import torch
     N = plan.N
+
+    def host_ptr(a, what, shape):
+        if hasattr(a, "data_ptr"):   # torch CPU tensor
+            if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float32" or tuple(a.shape) != shape:
+                raise ValueError(f"{what} must be a contiguous float32 CPU tensor of shape {shape}")
+            return ctypes.c_void_p(a.data_ptr())
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"] or a.shape != shape:
+            raise ValueError(f"{what} must be a C-contiguous float32 array of shape {shape}")
+        return ctypes.c_void_p(a.ctypes.data)
+
+    if not hasattr(proj_host, "data_ptr"):
+        proj_host = np.ascontiguousarray(proj_host, dtype=np.float32)
     if out is None:
         out = np.empty((N, N, N), dtype=np.float32)
-    bands = [(z0, min(slab, N - z0)) + plan.slab_rows(z0, min(slab, N - z0)) for z0 in range(0, N, slab)]
-    max_rows = max(b[3] for b in bands)
-    S = None
-    if plan.D > 1:
-        S = torch.empty(plan.slab_workspace_elems(max_rows), dtype=torch.float32, device="cuda")
-    for z0, nz, v0, nr in bands:
-        rows = torch.from_numpy(np.ascontiguousarray(proj_host[:, v0:v0 + nr, :])).cuda()
-        Q = plan.filter_rows(rows, v0)
-        vol = plan.backproject_slab(Q, v0, S, z0, nz)
-        out[z0:z0 + nz] = vol.cpu().numpy()
+    src = host_ptr(proj_host, "proj_host", (plan.P, plan.Nv, plan.Nu))
+    dst = host_ptr(out, "out", (N, N, N))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    used = ctypes.c_int64(0)
+    _check(load().fdkod_reconstruct_slabs(plan.handle, src, dst, int(slab), int(stream), ctypes.byref(used)),
+           "fdkod_reconstruct_slabs")
+    plan.last_slab_device_bytes = int(used.value)
     return out
