@@ -110,19 +110,34 @@ __device__ __forceinline__ constexpr int out_pos(int k) {
 // shared-memory index with one pad slot per 16 (breaks stride-16 conflicts)
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
-// One in-place Stockham pass of radix R over a buffer of length L (padded):
+// Where a pass leaves its output: in shared memory (kToSmem); in shared
+// memory times the ramp spectrum and conjugated (kToSpectrum, the last pass
+// of the forward transform: the inverse transform is the conjugate of a
+// forward one); or, for the first Nu samples, in the two output rows of Q
+// (kToQ, the last pass of the inverse transform).
+enum PassOut { kToSmem, kToSpectrum, kToQ };
+
+template <typename TQ>
+struct Sink {
+    const float *H;  // ramp spectrum / L
+    TQ *qa, *qb;     // output rows (nullptr: absent)
+    int Nu;
+};
+
+// One Stockham pass of radix R over a buffer of length L (padded):
 // item j reads R samples j + r L/R, twiddles them by
 // e^{-2 pi i r (j mod Ns) / (Ns R)}, does an R-point DFT and writes sample
 // r to (j - j mod Ns) R + (j mod Ns) + r Ns.  Each thread owns 16/R items
-// (16 values), all loaded before the barrier that precedes the stores.
+// (16 values), all loaded before the barrier that precedes in-place stores.
 // L, Ns and L/R are powers of two, so j mod Ns is a mask and the twiddle
 // index a shift; when the read stride L/R (write stride Ns) is a multiple of
 // 16, the padded index of sample r is the padded index of sample 0 plus r
 // times the padded stride, one add per sample.  Ns is 1 on the first pass
 // (its samples are consecutive within one 16-block) and a multiple of 16
 // after it.
-template <int R>
-__device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int lgL, int lgNs, int lt, int nt) {
+template <int R, int OUT, typename TQ>
+__device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int lgL, int lgNs, int lt, int nt,
+                                     const Sink<TQ> &sink) {
     constexpr int kItems = 16 / R;
     constexpr int lgR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
     const int n_items = 1 << (lgL - lgR);
@@ -132,7 +147,7 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw,
     const int pin = n_items + (n_items >> 4);  // its padded length
     const int pout = Ns + (Ns >> 4);           // padded write stride (Ns >= 16)
     float2 v[kItems][R];
-    int dst[kItems];
+    int d0[kItems];
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const int j = lt + it * nt;
@@ -165,32 +180,61 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw,
             for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
         }
         dft<R>(v[it]);
-        dst[it] = pad(((j - k) << lgR) + k);
+        d0[it] = ((j - k) << lgR) + k;
+    }
+    if (OUT == kToQ) {
+        // natural order after the last pass; only the first Nu samples are kept
+#pragma unroll
+        for (int it = 0; it < kItems; ++it)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = d0[it] + r * Ns;
+                if (i < sink.Nu) {
+                    const float2 x = v[it][out_pos<R>(r)];
+                    if (sink.qa) sink.qa[i] = to_q<TQ>(x.x);
+                    if (sink.qb) sink.qb[i] = to_q<TQ>(-x.y);
+                }
+            }
+        return;
     }
     __syncthreads();
     const int sstride = Ns == 1 ? 1 : pout;  // Ns = 1: R <= 16 consecutive samples of one 16-block
 #pragma unroll
-    for (int it = 0; it < kItems; ++it)
+    for (int it = 0; it < kItems; ++it) {
+        const int dp = pad(d0[it]);
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[dst[it] + r * sstride] = v[it][out_pos<R>(r)];
+        for (int r = 0; r < R; ++r) {
+            float2 x = v[it][out_pos<R>(r)];
+            if (OUT == kToSpectrum) {
+                const float h = __ldg(sink.H + d0[it] + r * Ns);
+                x = make_float2(x.x * h, -x.y * h);
+            }
+            buf[dp + r * sstride] = x;
+        }
+    }
     __syncthreads();
 }
 
-// Forward DFT of length L = 2^log2L (>= 16) in place: radix-16 passes, then
-// one pass of radix 2, 4 or 8 for the remaining factor.
-__device__ __forceinline__ void fft_forward(float2 *buf, const float2 *tw, int lgL, int lt, int nt) {
+// DFT of length L = 2^log2L (>= 16) in place: radix-16 passes, then one pass
+// of radix 2, 4 or 8 for the remaining factor; the last pass writes per OUT.
+template <int OUT, typename TQ>
+__device__ __forceinline__ void fft(float2 *buf, const float2 *tw, int lgL, int lt, int nt, const Sink<TQ> &sink) {
+    const int rest = lgL & 3;
+    const int n16 = lgL >> 2;
     int lgNs = 0;
-    while (lgNs + 4 <= lgL) {
-        pass<16>(buf, tw, lgL, lgNs, lt, nt);
+    for (int p = 0; p < n16; ++p) {
+        if (p == n16 - 1 && rest == 0) pass<16, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
+        else pass<16, kToSmem>(buf, tw, lgL, lgNs, lt, nt, sink);
         lgNs += 4;
     }
-    const int rest = lgL - lgNs;
-    if (rest == 3) pass<8>(buf, tw, lgL, lgNs, lt, nt);
-    else if (rest == 2) pass<4>(buf, tw, lgL, lgNs, lt, nt);
-    else if (rest == 1) pass<2>(buf, tw, lgL, lgNs, lt, nt);
+    if (rest == 3) pass<8, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
+    else if (rest == 2) pass<4, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
+    else if (rest == 1) pass<2, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
 }
 
-// G row pairs per CTA, L/16 threads per pair.
+// G row pairs per CTA, L/16 threads per pair: weighted rows into shared
+// memory, forward transform (times the spectrum on its last pass), inverse
+// transform (its last pass stores the rows of Q).
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
@@ -217,21 +261,13 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
         buf[pad(i)] = v;
     }
     __syncthreads();
-    fft_forward(buf, tw, lgL, lt, nt);
-    // product with the real, even ramp spectrum (1/L folded in), conjugated:
-    // the inverse transform is the conjugate of a forward transform
-    for (int i = lt; i < L; i += nt) {
-        const float h = __ldg(H + i);
-        const float2 v = buf[pad(i)];
-        buf[pad(i)] = make_float2(v.x * h, -v.y * h);
-    }
-    __syncthreads();
-    fft_forward(buf, tw, lgL, lt, nt);
-    for (int u = lt; u < Nu; u += nt) {
-        const float2 v = buf[pad(u)];
-        if (hasA) Q[rowA * Nu + u] = to_q<TQ>(v.x);
-        if (hasB) Q[rowB * Nu + u] = to_q<TQ>(-v.y);
-    }
+    Sink<TQ> sink;
+    sink.H = H;
+    sink.qa = hasA ? Q + rowA * Nu : nullptr;
+    sink.qb = hasB ? Q + rowB * Nu : nullptr;
+    sink.Nu = Nu;
+    fft<kToSpectrum>(buf, tw, lgL, lt, nt, sink);
+    fft<kToQ>(buf, tw, lgL, lt, nt, sink);
 }
 
 template <typename TQ>
