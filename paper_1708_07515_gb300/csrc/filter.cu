@@ -135,7 +135,10 @@ struct Sink {
 // times the padded stride, one add per sample.  Ns is 1 on the first pass
 // (its samples are consecutive within one 16-block) and a multiple of 16
 // after it.
-template <int R, int OUT, typename TQ>
+// FIRST: the forward transform's first pass (radix 16, Ns = 1), whose inputs
+// r >= 8 lie at j + r L/16 >= L/2 >= Nu, in the zero padding: they are
+// constant zeros, neither stored by the input stage nor loaded here.
+template <int R, int OUT, typename TQ, bool FIRST = false>
 __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw, int lgL, int lgNs, int lt, int nt,
                                      const Sink<TQ> &sink) {
     constexpr int kItems = 16 / R;
@@ -152,14 +155,17 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw,
     for (int it = 0; it < kItems; ++it) {
         const int j = lt + it * nt;
         const int k = j & (Ns - 1);
+        constexpr int kLoad = FIRST ? R / 2 : R;
         if (whole_in) {
             const int b0 = pad(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[it][r] = buf[b0 + r * pin];
+            for (int r = 0; r < kLoad; ++r) v[it][r] = buf[b0 + r * pin];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[it][r] = buf[pad(j + r * n_items)];
+            for (int r = 0; r < kLoad; ++r) v[it][r] = buf[pad(j + r * n_items)];
         }
+#pragma unroll
+        for (int r = kLoad; r < R; ++r) v[it][r] = make_float2(0.f, 0.f);
         if (Ns > 1) {
             float2 w[R];
             w[1] = tw[k << lg_tstep];
@@ -217,14 +223,22 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *__restrict__ tw,
 
 // DFT of length L = 2^log2L (>= 16) in place: radix-16 passes, then one pass
 // of radix 2, 4 or 8 for the remaining factor; the last pass writes per OUT.
+// The forward transform (OUT = kToSpectrum) starts on data whose upper half
+// is zero padding.
 template <int OUT, typename TQ>
 __device__ __forceinline__ void fft(float2 *buf, const float2 *tw, int lgL, int lt, int nt, const Sink<TQ> &sink) {
     const int rest = lgL & 3;
     const int n16 = lgL >> 2;
     int lgNs = 0;
     for (int p = 0; p < n16; ++p) {
-        if (p == n16 - 1 && rest == 0) pass<16, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
-        else pass<16, kToSmem>(buf, tw, lgL, lgNs, lt, nt, sink);
+        if (p == n16 - 1 && rest == 0) {
+            if (p == 0 && OUT == kToSpectrum) pass<16, OUT, TQ, true>(buf, tw, lgL, lgNs, lt, nt, sink);
+            else pass<16, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
+        } else if (p == 0 && OUT == kToSpectrum) {
+            pass<16, kToSmem, TQ, true>(buf, tw, lgL, lgNs, lt, nt, sink);
+        } else {
+            pass<16, kToSmem>(buf, tw, lgL, lgNs, lt, nt, sink);
+        }
         lgNs += 4;
     }
     if (rest == 3) pass<8, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
@@ -251,7 +265,7 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
     const float bA = (float)(row0 + (int)(rowA % rows_per_view)) - 0.5f * (float)(Nv - 1);
     const float bB = (float)(row0 + (int)(rowB % rows_per_view)) - 0.5f * (float)(Nv - 1);
     const float R2 = R * R;
-    for (int i = lt; i < L; i += nt) {
+    for (int i = lt; i < L / 2; i += nt) {  // the upper half is never read (see pass)
         float2 v = make_float2(0.f, 0.f);
         if (i < Nu) {
             const float u = (float)i - 0.5f * (float)(Nu - 1);
