@@ -16,6 +16,11 @@ Functions and the passages they follow:
   shift_decimate         shift + angular low-pass + downsample (Sec. 2.1)
   triangle_taps / sinc_taps   the angular low-pass kernels (default / windowed sinc)
   fdkod / fdkod_slices   FDK-OD (Sec. 2.2)
+  shift_rows             the shifted rows of one square at the full view rate
+                         (step 1 of Sec. 2.1 alone)
+  bp_square / bp_square_adjoint   backprojection of given decomposed data of
+                         one square (Sec. 2.2) and its adjoint
+  fdkod_net_slices       FDK-OD with the learned decimation of net.py
 
 Every function here has at least one pin in tests/test_oracle_*.py that does
 not go through the oracle itself.
@@ -72,6 +77,12 @@ def _load():
                                                  _c_int, _c_int, _vp, _vp, _vp, _c_int]),
                 "oracle_fdkod": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int,
                                           _vp, _vp, _c_int]),
+                "oracle_shift_rows": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int,
+                                               _c_int, _c_int, _c_int, _vp]),
+                "oracle_bp_square": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int,
+                                              _c_int, _vp, _vp]),
+                "oracle_bp_square_adjoint": (_c_int, [_c_double, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int,
+                                                      _vp, _c_int, _c_int, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -237,3 +248,56 @@ def fdkod(Q: np.ndarray, R: float, N: int, s: int, D: int, taps=None) -> np.ndar
     hp, H, _keep = _taps_arg(taps, D)
     _check(_load().oracle_fdkod(R, N, Nu, Nv, P, s, D, _ptr(Q), f64, _ptr(out), hp, H), "fdkod")
     return out
+
+
+def shift_rows(Q: np.ndarray, R: float, N: int, s: int, q: int, v0: int = 0, nv=None) -> np.ndarray:
+    """S_q[k][v - v0][t] at the full view rate (no low-pass), rows v0 .. v0 + nv - 1."""
+    Q, f64 = _qarg(Q)
+    P, Nv, Nu = Q.shape
+    nv = Nv - v0 if nv is None else nv
+    T = int(bounds(R, N, Nu, P, s)["T"][q])
+    out = np.empty((P, nv, T), dtype=np.float64)
+    _check(_load().oracle_shift_rows(R, N, Nu, Nv, P, s, _ptr(Q), f64, q, v0, nv, _ptr(out)), "shift_rows")
+    return out
+
+
+def bp_square(Sp: np.ndarray, R: float, N: int, Nu: int, P: int, s: int, D: int, q: int, zs) -> np.ndarray:
+    """Backprojection of decomposed data Sp[P/D][Nv][T_q] into square q's
+    voxels on slices zs; other voxels of the returned [nz][N][N] are 0."""
+    Sp = np.ascontiguousarray(Sp, dtype=np.float64)
+    Nv = Sp.shape[1]
+    zs = np.ascontiguousarray(zs, dtype=np.int32).reshape(-1)
+    out = np.zeros((zs.size, N, N), dtype=np.float64)
+    _check(_load().oracle_bp_square(R, N, Nu, Nv, P, s, D, _ptr(Sp), q, zs.size, _ptr(zs), _ptr(out)), "bp_square")
+    return out
+
+
+def bp_square_adjoint(E: np.ndarray, R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, q: int,
+                      zs) -> np.ndarray:
+    """Adjoint of bp_square: [P/D][Nv][T_q] from E[nz][N][N] (only square q's
+    voxels are read)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    zs = np.ascontiguousarray(zs, dtype=np.int32).reshape(-1)
+    T = int(bounds(R, N, Nu, P, s)["T"][q])
+    out = np.empty((P // D, Nv, T), dtype=np.float64)
+    _check(_load().oracle_bp_square_adjoint(R, N, Nu, Nv, P, s, D, _ptr(E), q, zs.size, _ptr(zs), _ptr(out)),
+           "bp_square_adjoint")
+    return out
+
+
+def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, taps=None) -> np.ndarray:
+    """Decomposed data of square q with the learned decimation: the plain
+    low-pass (shift_decimate) plus the net's output on the shifted rows."""
+    from .net import net_forward
+    S = shift_rows(Q, R, N, s, q)                      # [P][Nv][T]
+    return shift_decimate(Q, R, N, s, D, q, taps) + net_forward(S, D, w)
+
+
+def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, taps=None) -> np.ndarray:
+    """FDK-OD slices with the learned decimation (D > 1)."""
+    P, Nv, Nu = np.shape(Q)
+    zs = np.asarray(zs).reshape(-1)
+    vol = np.zeros((zs.size, N, N))
+    for q in range(4 ** s):
+        vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps), R, N, Nu, P, s, D, q, zs)
+    return vol

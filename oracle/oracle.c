@@ -426,6 +426,35 @@ int oracle_shift_decimate(double R, int N, int Nu, int Nv, int P, int s, int D,
     return bad ? ORACLE_ENOMEM : ORACLE_OK;
 }
 
+/* Sample position of voxel (x, y, z) in decimated view j of square q's
+ * decomposed data (Sec. 2.2): column t = u - phi - w0 (the shift back folded
+ * in), row v = z / U + (Nv-1)/2, and U (the weight is U^-2). */
+static void od_sample_pos(const odplan *o, const double *cs, int q, int j, double x, double y, double z,
+                          double *t, double *v, double *Uo) {
+    int k = j * o->D;
+    double cb = cs[2 * k], sb = cs[2 * k + 1];
+    double u = eq1_a(o->R, x, y, cb, sb) + 0.5 * (double)(o->Nu - 1);
+    double U = fdk_U(o->R, x, y, cb, sb);
+    *t = u - o->phi[(size_t)q * o->P + k] - (double)o->w0[q];
+    *v = z / U + 0.5 * (double)(o->Nv - 1);
+    *Uo = U;
+}
+
+/* One voxel of square q backprojected from its decomposed data
+ * sp[j][v][t] (j < P/D, Nv rows, T_q columns), scale pi / (P/D). */
+static double bp_decomposed_voxel(const odplan *o, const double *cs, qbuf sp, int q, double x, double y,
+                                  double z) {
+    int T = o->T[q], Nv = o->Nv;
+    double acc = 0.0;
+    for (int j = 0; j < o->Pd; ++j) {
+        double t, v, U;
+        od_sample_pos(o, cs, q, j, x, y, z, &t, &v, &U);
+        double val = bilerp(sp, (size_t)j * Nv * T, Nv, T, t, v);
+        acc += val / (U * U);
+    }
+    return (M_PI / (double)o->Pd) * acc;
+}
+
 /* FDK-OD backprojection of the requested z-slices (Sec. 2.2):
  *   D = 1: each square reads its crop [lo, hi] of Q directly (no shift);
  *          every column read is checked against the crop window;
@@ -470,7 +499,7 @@ int oracle_fdkod_slices(double R, int N, int Nu, int Nv, int P, int s, int D,
         int ix0, ix1, iy0, iy1;
         square_range(qx, s, N, &ix0, &ix1);
         square_range(qy, s, N, &iy0, &iy1);
-        int T = o.T[q], w0 = o.w0[q];
+        int T = o.T[q];
         double *Sp = NULL;
         if (D > 1) {
             Sp = (double *)calloc((size_t)Pd * Nv * T, sizeof(double));
@@ -529,17 +558,7 @@ int oracle_fdkod_slices(double R, int N, int Nu, int Nv, int P, int s, int D,
                     }
                     vol[((size_t)iz * N + iy) * N + ix] = (M_PI / (double)P) * acc;
                 } else {
-                    for (int j = 0; j < Pd; ++j) {
-                        int k = j * D;
-                        double cb = cs[2 * k], sb = cs[2 * k + 1];
-                        double u = eq1_a(R, x, y, cb, sb) + uc;
-                        double U = fdk_U(R, x, y, cb, sb);
-                        double t = u - o.phi[(size_t)q * P + k] - (double)w0;
-                        double v = z / U + vc;
-                        double val = bilerp(sp, (size_t)j * Nv * T, Nv, T, t, v);
-                        acc += val / (U * U);
-                    }
-                    vol[((size_t)iz * N + iy) * N + ix] = (M_PI / (double)Pd) * acc;
+                    vol[((size_t)iz * N + iy) * N + ix] = bp_decomposed_voxel(&o, cs, sp, q, x, y, z);
                 }
             }
         }
@@ -560,4 +579,125 @@ int oracle_fdkod(double R, int N, int Nu, int Nv, int P, int s, int D, const voi
     int rc = oracle_fdkod_slices(R, N, Nu, Nv, P, s, D, Q, q_f64, N, zs, vol, h, H);
     free(zs);
     return rc;
+}
+
+/* ------------------------------------- pieces for the learned decimation */
+
+/* Step 1 of Sec. 2.1 alone: the shifted rows of square q at the full view
+ * rate, S[k][v - v0][t] = Q_k(v, phi_k + w0 + t), t < T_q, for detector rows
+ * v0 .. v0 + nv - 1 (the input of a learned angular low-pass). */
+int oracle_shift_rows(double R, int N, int Nu, int Nv, int P, int s, const void *Q, int q_f64, int q, int v0,
+                      int nv, double *out) {
+    odplan o;
+    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, 1, NULL, 1);
+    if (rc) return rc;
+    if (q < 0 || q >= o.nsq || v0 < 0 || nv < 0 || v0 + nv > Nv) {
+        odplan_free(&o);
+        return ORACLE_EINVAL;
+    }
+    qbuf qb = {Q, q_f64};
+    int T = o.T[q], w0 = o.w0[q];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < P; ++k) {
+        double p = o.phi[(size_t)q * P + k];
+        for (int v = 0; v < nv; ++v) {
+            size_t off = ((size_t)k * Nv + (size_t)(v0 + v)) * Nu;
+            for (int t = 0; t < T; ++t)
+                out[((size_t)k * nv + v) * T + t] = lerp_row(qb, off, Nu, (p + (double)w0) + (double)t);
+        }
+    }
+    odplan_free(&o);
+    return ORACLE_OK;
+}
+
+static double *trig_table(int P) {
+    double *cs = (double *)malloc(sizeof(double) * 2 * (size_t)P);
+    if (!cs) return NULL;
+    for (int k = 0; k < P; ++k) {
+        cs[2 * k] = cos(beta_of(k, P));
+        cs[2 * k + 1] = sin(beta_of(k, P));
+    }
+    return cs;
+}
+
+/* Backprojection of given decomposed data Sp[j][v][t] of square q (j < P/D,
+ * all Nv rows, T_q columns) into the square's voxels on slices zs (Sec. 2.2,
+ * the same sum as oracle_fdkod_slices); vol[nz][N][N], only square q's
+ * voxels are written. */
+int oracle_bp_square(double R, int N, int Nu, int Nv, int P, int s, int D, const double *Sp, int q, int nz,
+                     const int *zs, double *vol) {
+    for (int i = 0; i < nz; ++i)
+        if (zs[i] < 0 || zs[i] >= N) return ORACLE_EINVAL;
+    odplan o;
+    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D, NULL, 1);
+    if (rc) return rc;
+    double *cs = trig_table(P);
+    if (q < 0 || q >= o.nsq || !cs) {
+        free(cs);
+        odplan_free(&o);
+        return cs ? ORACLE_EINVAL : ORACLE_ENOMEM;
+    }
+    int m = 1 << s, ix0, ix1, iy0, iy1;
+    square_range(q % m, s, N, &ix0, &ix1);
+    square_range(q / m, s, N, &iy0, &iy1);
+    qbuf sp = {Sp, 1};
+    long lines = (long)nz * (iy1 - iy0 + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long l = 0; l < lines; ++l) {
+        int iz = (int)(l / (iy1 - iy0 + 1)), iy = iy0 + (int)(l % (iy1 - iy0 + 1));
+        double z = centre(zs[iz], N), y = centre(iy, N);
+        for (int ix = ix0; ix <= ix1; ++ix)
+            vol[((size_t)iz * N + iy) * N + ix] = bp_decomposed_voxel(&o, cs, sp, q, centre(ix, N), y, z);
+    }
+    free(cs);
+    odplan_free(&o);
+    return ORACLE_OK;
+}
+
+/* Adjoint of oracle_bp_square: dSp[j][v][t] = sum over square q's voxels on
+ * slices zs of E[iz][y][x] times the weight with which sample (j, v, t)
+ * enters that voxel, (pi / (P/D)) U^-2 times its bilinear weight (samples
+ * outside [0, Nv) x [0, T_q) have none).  dSp is overwritten.  Serial: the
+ * scatter sums in voxel order. */
+int oracle_bp_square_adjoint(double R, int N, int Nu, int Nv, int P, int s, int D, const double *E, int q,
+                             int nz, const int *zs, double *dSp) {
+    for (int i = 0; i < nz; ++i)
+        if (zs[i] < 0 || zs[i] >= N) return ORACLE_EINVAL;
+    odplan o;
+    int rc = odplan_make(&o, R, N, Nu, Nv, P, s, D, NULL, 1);
+    if (rc) return rc;
+    double *cs = trig_table(P);
+    if (q < 0 || q >= o.nsq || !cs) {
+        free(cs);
+        odplan_free(&o);
+        return cs ? ORACLE_EINVAL : ORACLE_ENOMEM;
+    }
+    int m = 1 << s, ix0, ix1, iy0, iy1, T = o.T[q];
+    square_range(q % m, s, N, &ix0, &ix1);
+    square_range(q / m, s, N, &iy0, &iy1);
+    memset(dSp, 0, sizeof(double) * (size_t)o.Pd * Nv * T);
+    double scale = M_PI / (double)o.Pd;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = iy0; iy <= iy1; ++iy)
+            for (int ix = ix0; ix <= ix1; ++ix) {
+                double e = E[((size_t)iz * N + iy) * N + ix];
+                double x = centre(ix, N), y = centre(iy, N), z = centre(zs[iz], N);
+                for (int j = 0; j < o.Pd; ++j) {
+                    double t, v, U;
+                    od_sample_pos(&o, cs, q, j, x, y, z, &t, &v, &U);
+                    double c0 = floor(t), r0 = floor(v);
+                    double fc = t - c0, fr = v - r0;
+                    double g = scale * e / (U * U);
+                    double wt[2][2] = {{(1.0 - fr) * (1.0 - fc), (1.0 - fr) * fc}, {fr * (1.0 - fc), fr * fc}};
+                    for (int dr = 0; dr < 2; ++dr)
+                        for (int dc = 0; dc < 2; ++dc) {
+                            long rr = (long)r0 + dr, cc = (long)c0 + dc;
+                            if (rr >= 0 && rr < Nv && cc >= 0 && cc < T)
+                                dSp[((size_t)j * Nv + (size_t)rr) * T + (size_t)cc] += g * wt[dr][dc];
+                        }
+                }
+            }
+    free(cs);
+    odplan_free(&o);
+    return ORACLE_OK;
 }
