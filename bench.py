@@ -62,9 +62,13 @@ def parse():
                     help="slab-wise (piecemeal, Sec. 2.2) reconstruction from host buffers, this many slices per slab")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the filtered projections (arithmetic stays float32)")
-    ap.add_argument("--taps", choices=["triangle", "sinc", "learned"], default="triangle",
-                    help="angular low-pass of the decomposition (Sec. 2.1): triangle, Hann-windowed sinc, or taps "
-                         "fitted to full FDK on separate training scans before the run (learn.py)")
+    ap.add_argument("--taps", choices=["triangle", "sinc", "learned", "net"], default="triangle",
+                    help="angular low-pass of the decomposition (Sec. 2.1): triangle, Hann-windowed sinc, taps "
+                         "fitted to full FDK on separate training scans before the run (learn.py), or the triangle "
+                         "plus the learned residual net (tensor-core layer 2; weights from --net-weights)")
+    ap.add_argument("--net-weights", default=None,
+                    help="weights of the learned decimation (.npy, 1440 values, learn_net.py --out); default: "
+                         "the package's trained weights for this D if present, else seeded random weights")
     return ap.parse_args()
 
 
@@ -237,6 +241,42 @@ def stage_rooflines(w, info, stages, qtype, peaks):
     return out
 
 
+def net_weights(path, D, seed=11):
+    """(weights, source) of the learned decimation for --taps net."""
+    if path is None:
+        cand = os.path.join(ROOT, "paper_1708_07515_gb300", "net_weights", f"D{D}.npy")
+        if os.path.exists(cand):
+            path = cand
+    if path is not None:
+        return np.load(path).astype(np.float32), os.path.relpath(path, ROOT)
+    rng = np.random.default_rng(seed)
+    w = np.concatenate([rng.standard_normal(80) * 0.4, rng.standard_normal(1280) * 0.15,
+                        rng.standard_normal(80) * 0.01]).astype(np.float32)
+    return w, f"seeded random weights (seed {seed}; throughput does not depend on the values)"
+
+
+def net_roofline(w, info, T, stages, peaks):
+    """The learned decimation kernel: layer 2's tensor-core work (16 x 16 x 5
+    multiply-adds per full-rate shifted sample) against the measured dense
+    BF16 peak, and its FP32 CUDA-core work (layer 1: 80 multiply-adds per
+    sample; layer 3 and the plain low-pass per output) against the FP32 peak."""
+    samples = float(np.sum(T)) * w.Nv * w.P                 # full-rate shifted samples (T_q per square)
+    mma_flop = samples * 2 * 16 * 16 * 5
+    outs = float(np.sum(T)) * w.Nv * (w.P // w.D)
+    fp32_flop = samples * 2 * 80 + outs * 2 * (80 + 2 * w.D - 1)
+    t = stages["decompose"] * 1e-3
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    max_mhz = peaks.get("sm_max_mhz") or 2070.0
+    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    return {"kernel": "net_decompose_kernel", "samples_per_launch": samples,
+            "tensor": {"bound": "tensor", "flop": mma_flop, "achieved": mma_flop / t / 1e12, "peak": bf16,
+                       "unit": "TFLOP/s", "frac": mma_flop / t / 1e12 / bf16,
+                       "peak_note": "measured dense BF16, sustained (cuBLAS loop; the kernel runs inside a long step)" if peaks.get("bf16_tflops_sustained")
+                       else "fallback 1700 TFLOP/s (sustained)"},
+            "fp32": {"bound": "alu", "flop": fp32_flop, "achieved": fp32_flop / t / 1e12, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": fp32_flop / t / 1e12 / fp32_peak}}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -401,7 +441,13 @@ def main():
         zs_fit = np.linspace(w.N // 8, w.N - 1 - w.N // 8, 16).round().astype(int)
         taps = learn.learn(w.R, w.N, w.P, w.s, w.D, 2, train, zs_fit)
         del train
+    net_w = net_src = None
+    if taps == "net":
+        net_w, net_src = net_weights(args.net_weights, w.D)
+        taps = "triangle"
     plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=taps)
+    if net_w is not None:
+        plan.set_net(net_w)
     info = plan.info
     stream = torch.cuda.current_stream()
     proj_d = torch.from_numpy(proj).cuda()
@@ -535,8 +581,11 @@ def main():
         Qo = np.zeros((w.P, w.Nv, w.Nu))
         Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
         ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
-        ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
-                                     taps=None if args.taps == "triangle" else plan.taps)
+        if net_w is not None:
+            ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, a1_round="bf16")
+        else:
+            ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
+                                         taps=None if args.taps == "triangle" else plan.taps)
         g = vol_od[zs].astype(np.float64)
         extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(g - ref_od) / np.linalg.norm(ref_od))
         extra["rel_rmse_vs_fp64_fdk_oracle"] = float(np.linalg.norm(g - ref_fdk) / np.linalg.norm(ref_fdk))
@@ -598,6 +647,8 @@ def main():
             "roofline_smem": {"achieved": smem_ach, "peak": smem_peak, "unit": "GB/s", "frac": smem_ach / smem_peak,
                               "bytes_per_update": SMEM_BYTES_PER_UPDATE},
             "roofline_stages": stage_rooflines(w, info, stages, args.qtype, peaks),
+            **({"roofline_net": net_roofline(w, info, plan.bounds()["T"], stages, peaks), "net_weights": net_src}
+               if net_w is not None else {}),
             "stages_ms": stages,
             "plain_fdk": {"value": world * upd_eff / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "step": "filter + plain backprojection"},

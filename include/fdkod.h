@@ -318,6 +318,54 @@ int fdkod_set_decimation_taps(fdkod_plan_t *plan, const double *h, int n);
 int fdkod_get_decimation_taps(const fdkod_plan_t *plan, double *h, int cap);
 int fdkod_sinc_taps(int D, int H, double *h);
 
+/*
+ * Learned angular decimation (Sec. 2.1 leaves the low-pass open and says
+ * its implementation sets the quality).  With a net set, the decomposition
+ * of fdkod_backproject, fdkod_decompose and the slab-wise entry points makes
+ * each decimated view the plain low-pass above plus a residual network
+ * along the view axis, applied to every shifted column (v, t) of a square
+ * as a circular sequence x[k] over the orbit (C = 16 channels, 5 taps at
+ * offsets m - 2, cross-correlation, no biases):
+ *   a1[c][k] = max(0, sum_m W1[c][m] x[k+m-2])
+ *   a2[c][k] = max(0, sum_{c',m} W2[c][c'][m] a1[c'][k+m-2])
+ *   S'[j]   += sum_{c,m} W3[c][m] a2[c][jD+m-2]
+ * Weights: FDKOD_NET_SIZE floats, W1 [16][5], then W2 [16][16][5] (output
+ * channel, input channel, tap), then W3 [16][5].  Inference stores them as
+ * BF16 (round to nearest even), keeps a1 as BF16 and accumulates in FP32;
+ * layer 2 runs on the tensor cores.
+ *
+ * fdkod_set_decimation_net: copy w (host, not retained) into the plan; w
+ *   NULL removes the net (plain low-pass again).  Synchronous; call it
+ *   while no launch of this plan is in flight.  Errors: INVALID_ARG (n !=
+ *   FDKOD_NET_SIZE, non-finite values), UNSUPPORTED (D < 2 or D > 60),
+ *   OOM, CUDA.
+ * fdkod_get_decimation_net: the plan's BF16-rounded weights as floats into
+ *   w[0 .. min(FDKOD_NET_SIZE, cap)-1]; returns FDKOD_NET_SIZE, or 0 when
+ *   no net is set.
+ *
+ * Training support (FP32, asynchronous on `stream`, device pointers):
+ * fdkod_net_adjoint: the adjoint of the FDK-OD backprojection of decomposed
+ *   data (Sec. 2.2), one slice z: with e = vol_slice - ref_slice ([N][N],
+ *   y then x), adds to dS ([4^s][P/D][Nv][T_stride], the layout of
+ *   fdkod_decompose) for every voxel and decimated view j the term
+ *   (pi / (P/D)) U^-2 e times the bilinear weight of the sample the
+ *   backprojection reads, and adds sum e^2 to *sq_err.  dS then holds
+ *   the gradient of (1/2) sum e^2 with respect to the decomposed data.
+ * fdkod_net_backward: for detector rows row_lo .. row_hi - 1, recompute the
+ *   net's forward pass from Q (all rows, qtype) with the FP32 weights w
+ *   (device, FDKOD_NET_SIZE floats) and add to dW (device, same layout) the
+ *   gradient of sum dS . S' (dS as above, the gradient of the decimated
+ *   views).  Errors of both: INVALID_ARG (null pointers, z or rows out of
+ *   range, D < 2), UNSUPPORTED (D > 60), CUDA.
+ */
+#define FDKOD_NET_SIZE 1440
+int fdkod_set_decimation_net(fdkod_plan_t *plan, const float *w, int n);
+int fdkod_get_decimation_net(const fdkod_plan_t *plan, float *w, int cap);
+int fdkod_net_adjoint(fdkod_plan_t *plan, const float *vol_slice, const float *ref_slice, int z, float *dS,
+                      float *sq_err, uintptr_t stream);
+int fdkod_net_backward(fdkod_plan_t *plan, const void *Q, const float *w, const float *dS, int row_lo,
+                       int row_hi, float *dW, uintptr_t stream);
+
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);
 

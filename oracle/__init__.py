@@ -285,19 +285,56 @@ def bp_square_adjoint(E: np.ndarray, R: float, N: int, Nu: int, Nv: int, P: int,
     return out
 
 
-def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, taps=None) -> np.ndarray:
+def triangle_or(taps, D: int) -> np.ndarray:
+    return triangle_taps(D) if taps is None else np.asarray(taps, dtype=np.float64).reshape(-1)
+
+
+def slice_rows(R: float, N: int, Nv: int, zs) -> tuple[int, int]:
+    """First detector row and row count that slices zs can touch: U lies in
+    [1 - r/R, 1 + r/R] with r the largest in-slice radius (the rows the C
+    oracle's FDK-OD computes)."""
+    vc = 0.5 * (Nv - 1)
+    rmax = np.sqrt(2.0) * 0.5 * (N - 1)
+    lo, hi = Nv, -1
+    for z in np.asarray(zs).reshape(-1):
+        zc = float(z) - 0.5 * (N - 1)
+        va, vb = zc / (1.0 - rmax / R) + vc, zc / (1.0 + rmax / R) + vc
+        lo = min(lo, int(np.floor(min(va, vb))) - 1)
+        hi = max(hi, int(np.floor(max(va, vb))) + 2)
+    lo, hi = max(lo, 0), min(hi, Nv - 1)
+    return lo, max(0, hi - lo + 1)
+
+
+def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, taps=None,
+                   a1_round=None, rows=None) -> np.ndarray:
     """Decomposed data of square q with the learned decimation: the plain
-    low-pass (shift_decimate) plus the net's output on the shifted rows."""
+    low-pass plus the net's output on the shifted rows (a1_round: see
+    net.net_forward).  rows = (v0, nv) computes only those detector rows
+    (the rest of the returned [P/D][Nv][T_q] is 0), with the plain low-pass
+    taken as the circular FIR of the shifted rows (equal to shift_decimate,
+    tests/test_oracle_net.py)."""
     from .net import net_forward
-    S = shift_rows(Q, R, N, s, q)                      # [P][Nv][T]
-    return shift_decimate(Q, R, N, s, D, q, taps) + net_forward(S, D, w)
+    P, Nv, _ = np.shape(Q)
+    if rows is None:
+        S = shift_rows(Q, R, N, s, q)                  # [P][Nv][T]
+        return shift_decimate(Q, R, N, s, D, q, taps) + net_forward(S, D, w, a1_round)
+    v0, nv = rows
+    S = shift_rows(Q, R, N, s, q, v0, nv)
+    h = triangle_or(taps, D)
+    lin = sum(h[abs(i)] * np.roll(S, -i, axis=0)[::D] for i in range(-(h.size - 1), h.size))
+    out = np.zeros((P // D, Nv, S.shape[2]))
+    out[:, v0:v0 + nv] = lin + net_forward(S, D, w, a1_round)
+    return out
 
 
-def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, taps=None) -> np.ndarray:
-    """FDK-OD slices with the learned decimation (D > 1)."""
+def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, taps=None,
+                     a1_round=None) -> np.ndarray:
+    """FDK-OD slices with the learned decimation (D > 1); only the detector
+    rows the slices touch are decomposed."""
     P, Nv, Nu = np.shape(Q)
     zs = np.asarray(zs).reshape(-1)
+    rows = slice_rows(R, N, Nv, zs)
     vol = np.zeros((zs.size, N, N))
     for q in range(4 ** s):
-        vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps), R, N, Nu, P, s, D, q, zs)
+        vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps, a1_round, rows), R, N, Nu, P, s, D, q, zs)
     return vol

@@ -26,6 +26,8 @@ Functions:
   net_vjp(x, D, w, dy)         gradient of sum(dy * y) with respect to w
   net_loop(x, D, w)            the same forward with explicit loops (tiny
                                inputs; an independent restatement for pins)
+  round_bf16, a1_rounding_bound   BF16 storage of a1 (the tensor-core
+                               operand) and a bound on what it changes
 Pins in tests/test_oracle_net.py.
 """
 from __future__ import annotations
@@ -58,11 +60,24 @@ def _ahead(a, d):
     return np.roll(a, -d, axis=1)
 
 
-def _layers(x, w):
+def round_bf16(a):
+    """Nearest value with an 8-bit significand (BF16), ties to even,
+    computed exactly in FP64 (normal range)."""
+    a = np.asarray(a, dtype=np.float64)
+    _, e = np.frexp(a)                                  # a = f 2^e, 0.5 <= |f| < 1
+    scale = np.ldexp(1.0, e - 8)
+    return np.round(a / scale) * scale
+
+
+def _layers(x, w, a1_round=None):
     W1, W2, W3 = net_unpack(w)
     x = np.asarray(x, dtype=np.float64)[None]          # [1][P][...]
     z1 = sum(W1[:, m].reshape((C, 1) + (1,) * (x.ndim - 2)) * _ahead(x, m - 2) for m in range(K))
     a1 = np.maximum(z1, 0.0)
+    if a1_round == "bf16":
+        a1 = round_bf16(a1)
+    elif a1_round is not None:
+        raise ValueError(f"unknown a1_round {a1_round!r}")
     z2 = np.zeros_like(a1)
     for m in range(K):
         z2 += np.tensordot(W2[:, :, m], _ahead(a1, m - 2), axes=(1, 0))
@@ -70,9 +85,10 @@ def _layers(x, w):
     return x, z1, a1, z2, a2, W3
 
 
-def net_forward(x, D: int, w) -> np.ndarray:
-    """y[j][...] for sequences x[P][...] (P divisible by D)."""
-    x, _, _, _, a2, W3 = _layers(x, w)
+def net_forward(x, D: int, w, a1_round=None) -> np.ndarray:
+    """y[j][...] for sequences x[P][...] (P divisible by D).  a1_round="bf16"
+    rounds a1 to BF16 (the storage of the tensor-core operand) before layer 2."""
+    x, _, _, _, a2, W3 = _layers(x, w, a1_round)
     P = x.shape[1]
     if P % D:
         raise ValueError("D must divide P")
@@ -155,3 +171,17 @@ def linear_net(g3, offsets=(1, -2), chans=(3, 11, 5, 9)) -> np.ndarray:
     W3[cc, :] = g3
     W3[cd, :] = -np.asarray(g3, np.float64)
     return net_pack(W1, W2, W3)
+
+
+def a1_rounding_bound(x, D: int, w, u: float = 2.0 ** -8) -> np.ndarray:
+    """Elementwise bound on the change of net_forward(x, D, w) when every a1
+    value is rounded with relative error at most u (a1 stored in a format of
+    unit roundoff u): ReLU is 1-Lipschitz, so the change is at most
+    u sum_{c,m} |W3| sum_{c',m'} |W2| |a1| at the output positions."""
+    x, _, a1, _, _, _ = _layers(x, w)
+    _, W2, W3 = net_unpack(w)
+    e2 = np.zeros_like(a1)
+    for m in range(K):
+        e2 += np.tensordot(np.abs(W2[:, :, m]), _ahead(a1, m - 2), axes=(1, 0))
+    full = sum(np.tensordot(np.abs(W3[:, m]), _ahead(e2, m - 2), axes=(0, 0)) for m in range(K))
+    return u * full[::D]

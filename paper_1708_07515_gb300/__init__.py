@@ -9,6 +9,7 @@ from .fdkod import (  # noqa: F401
     FDKOD_BF16,
     FDKOD_F16,
     FDKOD_F32,
+    FDKOD_NET_SIZE,
     FdkodError,
     Plan,
     fdk_backproject_plain,
@@ -19,8 +20,12 @@ from .fdkod import (  # noqa: F401
     fdkod_decompose,
     fdkod_filter,
     fdkod_get_bounds,
+    fdkod_get_decimation_net,
     fdkod_get_decimation_taps,
+    fdkod_net_adjoint,
+    fdkod_net_backward,
     fdkod_plan,
+    fdkod_set_decimation_net,
     fdkod_set_decimation_taps,
     fdkod_sinc_taps,
     lib_path,

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdkod.so")
 
-SOURCES = ["api.cu", "bounds.cu", "filter.cu", "decompose.cu", "backproject.cu", "noalloc.cu", "slabs.cu"]
+SOURCES = ["api.cu", "bounds.cu", "filter.cu", "decompose.cu", "backproject.cu", "noalloc.cu", "slabs.cu",
+           "netdec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 PER_FILE = {"bounds.cu": ["-fmad=false"]}

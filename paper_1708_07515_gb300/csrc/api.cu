@@ -55,6 +55,7 @@ void free_plan(PlanImpl &p) {
     cudaFree(p.tw);
     cudaFree(p.Sp);
     cudaFree(p.tapw);
+    cudaFree(p.net);
     cudaFree(p.status);
 }
 
@@ -498,6 +499,7 @@ int fdkod_set_decimation_taps(fdkod_plan_t *plan, const double *h, int n) {
         return FDKOD_ERR_CUDA;
     p.tap_blocks = n / p.D;
     for (int i = 0; i < 2 * fdkod::kMaxTapD; ++i) p.htaps[i] = i < n ? h[i] : 0.0;
+    if (p.net && upload_net(p) != cudaSuccess) return FDKOD_ERR_CUDA;
     return FDKOD_OK;
 }
 

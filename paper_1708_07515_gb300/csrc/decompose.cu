@@ -464,6 +464,7 @@ cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st
 
 cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b) {
     const int nrows = b.nrows < 0 ? p.g.Nv : b.nrows;
+    if (p.net) return launch_net_decompose(p, Q, out, st, nrows);
     switch (p.qtype) {
         case FDKOD_F32: return launch_t(p, (const float *)Q, out, st, nrows);
         case FDKOD_BF16: return launch_t(p, (const __nv_bfloat16 *)Q, out, st, nrows);

@@ -48,6 +48,21 @@ constexpr int kViewsPerChunk = 8;  // generic backprojection kernel
 constexpr int kViewsPerStage = 4;  // TMA backprojection kernel (two stages)
 constexpr int kMaxTapD = 128;      // largest decimation factor with a tap table
 
+// learned angular decimation: 16 channels, 5 taps, 1440 weights
+constexpr int kNetChannels = 16, kNetTaps = 5;
+constexpr int kNetSize = kNetChannels * kNetTaps * (kNetChannels + 2);
+constexpr int kNetMaxD = 60;  // one output view per 64-view chunk needs D <= 60
+// Device copy of the learned decimation's weights, BF16-rounded: layer 2 as
+// the tensor-core B operands (tap m: 16 output x 16 input channels, K-major,
+// two 8-channel planes of 256 bytes), layers 1 and 3 as floats, plus the
+// plain low-pass taps h[|i|] it adds to.
+struct __align__(16) NetWeights {
+    uint16_t w2[kNetTaps * 256];
+    float w1[kNetChannels * kNetTaps];
+    float w3[kNetChannels * kNetTaps];
+    float h[2 * kMaxTapD];
+};
+
 struct PlanImpl {
     fdkod_geometry g{};
     int s = 0, D = 1, Pd = 1;
@@ -66,6 +81,10 @@ struct PlanImpl {
     int tap_blocks = 1;
     double htaps[2 * kMaxTapD] = {};
     float4 *tapw = nullptr;
+    // learned decimation (null: the plain low-pass); net_host holds the
+    // BF16-rounded weights as floats in the layout of the C interface
+    NetWeights *net = nullptr;
+    float net_host[kNetSize] = {};
     // decomposed data S'[q][j][v][t]
     float *Sp = nullptr;
     int Tstride = 0;
@@ -122,6 +141,9 @@ struct Band {
 cudaError_t launch_bounds(const PlanImpl &p, SquareSet &ss, cudaStream_t st);
 cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b = Band{});
 cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b = Band{});
+cudaError_t launch_net_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, int nrows);
+// host: refresh the device copy of the net (weights from net_host, taps from htaps)
+cudaError_t upload_net(PlanImpl &p);
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
                                float *vol, cudaStream_t st, Band b = Band{});
 

@@ -74,6 +74,10 @@ def load():
                 "fdkod_get_decimation_taps": (i, [vp, vp, i]),
                 "fdkod_sinc_taps": (i, [i, i, vp]),
                 "fdkod_reconstruct_slabs": (i, [vp, vp, vp, i, u, ctypes.POINTER(ctypes.c_int64)]),
+                "fdkod_set_decimation_net": (i, [vp, vp, i]),
+                "fdkod_get_decimation_net": (i, [vp, vp, i]),
+                "fdkod_net_adjoint": (i, [vp, vp, vp, i, vp, vp, u]),
+                "fdkod_net_backward": (i, [vp, vp, vp, vp, i, i, vp, u]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -108,6 +112,7 @@ def _dev_ptr(t, what):
 
 FDKOD_PLAN_NO_WORKSPACE = 1
 FDKOD_PLAN_SINC_TAPS = 2
+FDKOD_NET_SIZE = 1440
 
 
 def fdkod_plan(R: float, N: int, Nu: int, Nv: int, P: int, s: int, D: int, qtype: int = FDKOD_F32,
@@ -188,6 +193,35 @@ def fdkod_get_decimation_taps(plan: int) -> np.ndarray:
     h = np.empty(n, np.float64)
     load().fdkod_get_decimation_taps(plan, ctypes.c_void_p(h.ctypes.data), n)
     return h
+
+
+def fdkod_set_decimation_net(plan: int, w) -> None:
+    """Set (w: FDKOD_NET_SIZE values) or remove (w None) the learned decimation."""
+    if w is None:
+        _check(load().fdkod_set_decimation_net(plan, None, 0), "fdkod_set_decimation_net")
+        return
+    a = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+    _check(load().fdkod_set_decimation_net(plan, ctypes.c_void_p(a.ctypes.data), a.size),
+           "fdkod_set_decimation_net")
+
+
+def fdkod_get_decimation_net(plan: int):
+    """The plan's BF16-rounded net weights (float32), or None without a net."""
+    a = np.empty(FDKOD_NET_SIZE, np.float32)
+    n = load().fdkod_get_decimation_net(plan, ctypes.c_void_p(a.ctypes.data), a.size)
+    _check(min(n, 0), "fdkod_get_decimation_net")
+    return a if n > 0 else None
+
+
+def fdkod_net_adjoint(plan: int, vol_slice, ref_slice, z: int, dS, sq_err, stream=None) -> None:
+    _check(load().fdkod_net_adjoint(plan, _dev_ptr(vol_slice, "vol_slice"), _dev_ptr(ref_slice, "ref_slice"), int(z),
+                                    _dev_ptr(dS, "dS"), _dev_ptr(sq_err, "sq_err"), _stream(dS, stream)),
+           "fdkod_net_adjoint")
+
+
+def fdkod_net_backward(plan: int, Q, w, dS, row_lo: int, row_hi: int, dW, stream=None) -> None:
+    _check(load().fdkod_net_backward(plan, _dev_ptr(Q, "Q"), _dev_ptr(w, "w"), _dev_ptr(dS, "dS"), int(row_lo),
+                                     int(row_hi), _dev_ptr(dW, "dW"), _stream(dS, stream)), "fdkod_net_backward")
 
 
 # ---- convenience wrapper --------------------------------------------------
@@ -317,6 +351,21 @@ class Plan:
     def set_taps(self, taps) -> None:
         """Replace the angular low-pass taps (D or 2D values h[|i|])."""
         fdkod_set_decimation_taps(self.handle, taps)
+
+    @property
+    def net(self):
+        """The learned decimation's weights (BF16-rounded), or None."""
+        return fdkod_get_decimation_net(self.handle)
+
+    def set_net(self, w) -> None:
+        """Set (FDKOD_NET_SIZE weights) or remove (None) the learned decimation."""
+        fdkod_set_decimation_net(self.handle, w)
+
+    def net_adjoint(self, vol_slice, ref_slice, z: int, dS, sq_err, stream=None) -> None:
+        fdkod_net_adjoint(self.handle, vol_slice, ref_slice, z, dS, sq_err, stream)
+
+    def net_backward(self, Q, w, dS, row_lo: int, row_hi: int, dW, stream=None) -> None:
+        fdkod_net_backward(self.handle, Q, w, dS, row_lo, row_hi, dW, stream)
 
     def bounds(self) -> dict:
         return fdkod_get_bounds(self.handle, self.info["n_squares"], self.P)

@@ -1,0 +1,206 @@
+"""Training of the learned angular decimation (the residual conv net of
+fdkod_set_decimation_net) with the library's own kernels.
+
+Sec. 2.1 leaves the angular low-pass open and says its implementation sets
+the quality; full FDK (D = 1, the same decomposition without decimation)
+is the reconstruction FDK-OD approximates, so it is the target.  Per step,
+for one training scan (filtered projections Q on the device) and a batch of
+slices:
+
+  1. S' = the decomposition with the current weights (the tensor-core
+     inference kernel: BF16 weights, BF16 a1, FP32 accumulation);
+  2. f = the FDK-OD backprojection of S';
+  3. per slice z, fdkod_net_adjoint turns e = f[z] - f_FDK[z] into dS, the
+     gradient of (1/2) sum e^2 with respect to S';
+  4. fdkod_net_backward turns dS into the weight gradient (FP32 master
+     weights, forward recomputed in FP32: the BF16 rounding of inference is
+     passed straight through);
+  5. Adam on the 1440 master weights (host).
+
+The loss is sum e^2 / sum f_FDK^2 over the step's slices.  Layer 3 starts
+at zero, so training starts from the plain low-pass.
+
+    python -m paper_1708_07515_gb300.learn_net --N 512 --P 720 --s 3 --D 4
+
+prints the loss curve, the held-out rel-RMSE against full FDK of the
+triangle, the windowed sinc and the net, and writes the weights (--out).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+NET_SIZE = 1440
+
+
+def init_weights(seed: int) -> np.ndarray:
+    """He-scaled layers 1 and 2, layer 3 zero (the plain low-pass)."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.standard_normal(80) * np.sqrt(2.0 / 5.0)
+    w2 = rng.standard_normal(1280) * np.sqrt(2.0 / 80.0)
+    return np.concatenate([w1, w2, np.zeros(80)]).astype(np.float32)
+
+
+class Adam:
+    def __init__(self, n: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self.m = np.zeros(n)
+        self.v = np.zeros(n)
+        self.t = 0
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+
+    def step(self, w: np.ndarray, g: np.ndarray) -> np.ndarray:
+        self.t += 1
+        self.m = self.b1 * self.m + (1 - self.b1) * g
+        self.v = self.b2 * self.v + (1 - self.b2) * g * g
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        return (w - self.lr * mh / (np.sqrt(vh) + self.eps)).astype(np.float32)
+
+
+def merge_rows(ranges):
+    """Union of half-open row intervals as disjoint intervals."""
+    out = []
+    for lo, hi in sorted(ranges):
+        if out and lo <= out[-1][1]:
+            out[-1][1] = max(out[-1][1], hi)
+        else:
+            out.append([lo, hi])
+    return [tuple(r) for r in out]
+
+
+class Trainer:
+    """Holds one plan (R, N, P, s, D), the training scans' Q and FDK volumes."""
+
+    def __init__(self, R: float, N: int, P: int, s: int, D: int, taps="triangle"):
+        import torch
+
+        from .fdkod import Plan
+        self.torch = torch
+        self.N, self.P, self.D = N, P, D
+        self.plan = Plan(R, N, N, N, P, s, D, taps=taps)
+        self.ref_plan = Plan(R, N, N, N, P, s, 1)
+        info = self.plan.info
+        self.dS = torch.zeros((info["n_squares"], info["Pd"], N, info["T_stride"]), device="cuda")
+        self.dW = torch.zeros(NET_SIZE, device="cuda")
+        self.err = torch.zeros(1, device="cuda")
+        self.wdev = torch.zeros(NET_SIZE, device="cuda")
+        self.scans = []
+
+    def close(self):
+        self.plan.close()
+        self.ref_plan.close()
+
+    def add_scan(self, proj):
+        """proj: unfiltered projections [P][N][N] (torch CUDA float32)."""
+        Q = self.plan.filter(proj)
+        ref = self.ref_plan.backproject(Q)
+        self.scans.append((Q, ref))
+
+    def loss_and_grad(self, w: np.ndarray, scan: int, zs) -> tuple[float, np.ndarray]:
+        torch = self.torch
+        Q, ref = self.scans[scan]
+        self.plan.set_net(w)
+        S = self.plan.decompose(Q)
+        vol = self.plan.backproject_decomposed(S)
+        self.dS.zero_()
+        self.dW.zero_()
+        self.err.zero_()
+        for z in zs:
+            self.plan.net_adjoint(vol[z], ref[z], int(z), self.dS, self.err)
+        rows = merge_rows([(v0, v0 + n) for v0, n in (self.plan.slab_rows(int(z), 1) for z in zs)])
+        self.wdev.copy_(torch.from_numpy(w))
+        for lo, hi in rows:
+            self.plan.net_backward(Q, self.wdev, self.dS, lo, hi, self.dW)
+        den = float(sum(torch.sum(ref[z].double() ** 2).item() for z in zs))
+        loss = self.err.item() / den
+        return loss, self.dW.cpu().numpy().astype(np.float64) * (2.0 / den)
+
+    def rel_rmse(self, w, scans, zs) -> float:
+        """rel-RMSE against full FDK on the given scans and slices (w None:
+        the plain low-pass)."""
+        torch = self.torch
+        self.plan.set_net(w)
+        num = den = 0.0
+        for Q, ref in scans:
+            vol = self.plan.backproject(Q)
+            for z in zs:
+                num += float(torch.sum((vol[z].double() - ref[z].double()) ** 2).item())
+                den += float(torch.sum(ref[z].double() ** 2).item())
+        self.plan.set_net(None)
+        return (num / den) ** 0.5
+
+
+def train(tr: Trainer, steps: int, lr: float, slices: int, seed: int, w0=None, log_every: int = 10):
+    rng = np.random.default_rng(seed)
+    w = init_weights(seed) if w0 is None else np.asarray(w0, np.float32)
+    opt = Adam(NET_SIZE, lr)
+    N = tr.N
+    curve = []
+    for it in range(steps):
+        scan = it % len(tr.scans)
+        zs = rng.integers(N // 10, N - N // 10, size=slices)
+        loss, g = tr.loss_and_grad(w, scan, zs)
+        w = opt.step(w, g)
+        if it % log_every == 0 or it == steps - 1:
+            curve.append((it, loss))
+    return w, curve
+
+
+def main(argv=None):
+    import torch
+
+    import phantom
+    from .fdkod import fdkod_sinc_taps
+
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--P", type=int, default=720)
+    ap.add_argument("--s", type=int, default=3)
+    ap.add_argument("--D", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--slices", type=int, default=4, help="slices per step")
+    ap.add_argument("--train", type=int, default=4, help="training scans (seeds 8000..)")
+    ap.add_argument("--test", type=int, default=2, help="held-out scans (seeds 9000..)")
+    ap.add_argument("--ellipsoids", type=int, default=40)
+    ap.add_argument("--eval-slices", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--out", default=None, help="write the trained weights here (.npy)")
+    args = ap.parse_args(argv)
+    N, P, s, D = args.N, args.P, args.s, args.D
+    R = 4.0 * N
+    torch.cuda.set_device(0)
+
+    def scan(seed):
+        return phantom.project_gpu(phantom.make_phantom(seed, N, args.ellipsoids), R, N, N, P)
+
+    tr = Trainer(R, N, P, s, D)
+    try:
+        for i in range(args.train):
+            tr.add_scan(scan(8000 + i))
+        t0 = time.time()
+        w, curve = train(tr, args.steps, args.lr, args.slices, args.seed)
+        t_train = time.time() - t0
+        held = []
+        for i in range(args.test):
+            tr.add_scan(scan(9000 + i))
+            held.append(tr.scans.pop())
+        zs = np.linspace(N // 8, N - 1 - N // 8, args.eval_slices).round().astype(int)
+        errs = {"triangle": tr.rel_rmse(None, held, zs), "net": tr.rel_rmse(w, held, zs)}
+        tr.plan.set_taps(fdkod_sinc_taps(D, 2))
+        errs["sinc"] = tr.rel_rmse(None, held, zs)
+    finally:
+        tr.close()
+    if args.out:
+        np.save(args.out, w)
+    print(json.dumps({"N": N, "P": P, "s": s, "D": D, "steps": args.steps, "train_scans": args.train,
+                      "held_out_scans": args.test, "train_seconds": round(t_train, 2),
+                      "loss_curve": [(i, float(f"{l:.4e}")) for i, l in curve],
+                      "rel_rmse_vs_fdk": errs}))
+
+
+if __name__ == "__main__":
+    main()

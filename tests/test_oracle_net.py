@@ -186,3 +186,28 @@ def test_linear_net_pipeline_equals_fdkod_with_summed_taps(oracle_mod, D, offset
             fir = sum(g * np.roll(S, -i, axis=0) for i, g in comp.items())[::D]
             want += oracle_mod.bp_square(fir, R, N, N, P, s, D, q, zs)
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_round_bf16_matches_the_format():
+    """Values with 8 significant bits are fixed points; midpoints go to the
+    even neighbour; the relative change is at most 2^-8."""
+    exact = np.array([1.0, 1.5, 1.9921875, 3.0, 0.75, 2.0 ** -20 * 1.25, 255.0, 256.0])
+    np.testing.assert_array_equal(net.round_bf16(exact), exact)
+    # 1 + 2^-8 is the midpoint between 1 and 1 + 2^-7: ties to even (1)
+    assert net.round_bf16(1.0 + 2.0 ** -8) == 1.0
+    assert net.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2 * 2.0 ** -7     # midpoint, odd below
+    assert net.round_bf16(1.0 + 2.0 ** -8 + 2.0 ** -30) == 1.0 + 2.0 ** -7
+    a = np.random.default_rng(50).uniform(1e-3, 1e3, 10000)
+    r = net.round_bf16(a)
+    assert np.all(np.abs(r - a) <= 2.0 ** -8 * a)
+    f = np.frexp(r)[0] * 256.0                          # significand as an integer
+    assert np.all(f == np.round(f))
+
+
+def test_a1_rounding_bound_covers_bf16_storage():
+    rng = np.random.default_rng(51)
+    x = rng.standard_normal((48, 30))
+    w = _rand_net(52)
+    d = np.abs(net.net_forward(x, 4, w, a1_round="bf16") - net.net_forward(x, 4, w))
+    assert np.all(d <= net.a1_rounding_bound(x, 4, w))
+    assert d.max() > 0
