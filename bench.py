@@ -582,7 +582,7 @@ def main():
         Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
         ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
         if net_w is not None:
-            ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, a1_round="bf16")
+            ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, act_round="bf16")
         else:
             ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
                                          taps=None if args.taps == "triangle" else plan.taps)

@@ -306,9 +306,9 @@ def slice_rows(R: float, N: int, Nv: int, zs) -> tuple[int, int]:
 
 
 def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, taps=None,
-                   a1_round=None, rows=None) -> np.ndarray:
+                   act_round=None, rows=None) -> np.ndarray:
     """Decomposed data of square q with the learned decimation: the plain
-    low-pass plus the net's output on the shifted rows (a1_round: see
+    low-pass plus the net's output on the shifted rows (act_round: see
     net.net_forward).  rows = (v0, nv) computes only those detector rows
     (the rest of the returned [P/D][Nv][T_q] is 0), with the plain low-pass
     taken as the circular FIR of the shifted rows (equal to shift_decimate,
@@ -317,18 +317,18 @@ def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, t
     P, Nv, _ = np.shape(Q)
     if rows is None:
         S = shift_rows(Q, R, N, s, q)                  # [P][Nv][T]
-        return shift_decimate(Q, R, N, s, D, q, taps) + net_forward(S, D, w, a1_round)
+        return shift_decimate(Q, R, N, s, D, q, taps) + net_forward(S, D, w, act_round)
     v0, nv = rows
     S = shift_rows(Q, R, N, s, q, v0, nv)
     h = triangle_or(taps, D)
     lin = sum(h[abs(i)] * np.roll(S, -i, axis=0)[::D] for i in range(-(h.size - 1), h.size))
     out = np.zeros((P // D, Nv, S.shape[2]))
-    out[:, v0:v0 + nv] = lin + net_forward(S, D, w, a1_round)
+    out[:, v0:v0 + nv] = lin + net_forward(S, D, w, act_round)
     return out
 
 
 def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, taps=None,
-                     a1_round=None) -> np.ndarray:
+                     act_round=None) -> np.ndarray:
     """FDK-OD slices with the learned decimation (D > 1); only the detector
     rows the slices touch are decomposed."""
     P, Nv, Nu = np.shape(Q)
@@ -336,5 +336,5 @@ def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, tap
     rows = slice_rows(R, N, Nv, zs)
     vol = np.zeros((zs.size, N, N))
     for q in range(4 ** s):
-        vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps, a1_round, rows), R, N, Nu, P, s, D, q, zs)
+        vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps, act_round, rows), R, N, Nu, P, s, D, q, zs)
     return vol

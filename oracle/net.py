@@ -26,8 +26,8 @@ Functions:
   net_vjp(x, D, w, dy)         gradient of sum(dy * y) with respect to w
   net_loop(x, D, w)            the same forward with explicit loops (tiny
                                inputs; an independent restatement for pins)
-  round_bf16, a1_rounding_bound   BF16 storage of a1 (the tensor-core
-                               operand) and a bound on what it changes
+  round_bf16, act_rounding_bound  BF16 storage of the layers' inputs (the
+                               tensor-core operands) and a bound on what it changes
 Pins in tests/test_oracle_net.py.
 """
 from __future__ import annotations
@@ -69,26 +69,28 @@ def round_bf16(a):
     return np.round(a / scale) * scale
 
 
-def _layers(x, w, a1_round=None):
+def _layers(x, w, act_round=None):
+    """x, z1, a1, z2, a2, W3; act_round="bf16" rounds every layer's input
+    (x, a1, a2) to BF16, the operands of a tensor-core evaluation."""
+    if act_round not in (None, "bf16"):
+        raise ValueError(f"unknown act_round {act_round!r}")
+    rnd = round_bf16 if act_round == "bf16" else (lambda a: a)
     W1, W2, W3 = net_unpack(w)
-    x = np.asarray(x, dtype=np.float64)[None]          # [1][P][...]
+    x = rnd(np.asarray(x, dtype=np.float64)[None])     # [1][P][...]
     z1 = sum(W1[:, m].reshape((C, 1) + (1,) * (x.ndim - 2)) * _ahead(x, m - 2) for m in range(K))
-    a1 = np.maximum(z1, 0.0)
-    if a1_round == "bf16":
-        a1 = round_bf16(a1)
-    elif a1_round is not None:
-        raise ValueError(f"unknown a1_round {a1_round!r}")
+    a1 = rnd(np.maximum(z1, 0.0))
     z2 = np.zeros_like(a1)
     for m in range(K):
         z2 += np.tensordot(W2[:, :, m], _ahead(a1, m - 2), axes=(1, 0))
-    a2 = np.maximum(z2, 0.0)
+    a2 = rnd(np.maximum(z2, 0.0))
     return x, z1, a1, z2, a2, W3
 
 
-def net_forward(x, D: int, w, a1_round=None) -> np.ndarray:
-    """y[j][...] for sequences x[P][...] (P divisible by D).  a1_round="bf16"
-    rounds a1 to BF16 (the storage of the tensor-core operand) before layer 2."""
-    x, _, _, _, a2, W3 = _layers(x, w, a1_round)
+def net_forward(x, D: int, w, act_round=None) -> np.ndarray:
+    """y[j][...] for sequences x[P][...] (P divisible by D).  act_round="bf16"
+    rounds x, a1 and a2 to BF16 (the tensor-core operands) before the layer
+    that reads them."""
+    x, _, _, _, a2, W3 = _layers(x, w, act_round)
     P = x.shape[1]
     if P % D:
         raise ValueError("D must divide P")
@@ -173,15 +175,21 @@ def linear_net(g3, offsets=(1, -2), chans=(3, 11, 5, 9)) -> np.ndarray:
     return net_pack(W1, W2, W3)
 
 
-def a1_rounding_bound(x, D: int, w, u: float = 2.0 ** -8) -> np.ndarray:
-    """Elementwise bound on the change of net_forward(x, D, w) when every a1
-    value is rounded with relative error at most u (a1 stored in a format of
-    unit roundoff u): ReLU is 1-Lipschitz, so the change is at most
-    u sum_{c,m} |W3| sum_{c',m'} |W2| |a1| at the output positions."""
-    x, _, a1, _, _, _ = _layers(x, w)
-    _, W2, W3 = net_unpack(w)
+def act_rounding_bound(x, D: int, w, u: float = 2.0 ** -8) -> np.ndarray:
+    """Elementwise bound, to first order in u, on the change of
+    net_forward(x, D, w) when every x, a1 and a2 value is rounded with
+    relative error at most u (storage of unit roundoff u): ReLU is
+    1-Lipschitz and each layer is linear in its input, so the change is at
+    most u (|W3| |a2| + |W3| |W2| |a1| + |W3| |W2| |W1| |x|) at the output
+    positions, |W| the layers with absolute weights; the factor 1 + 4u
+    absorbs the higher-order terms."""
+    x, _, a1, _, a2, _ = _layers(x, w)
+    W1, W2, W3 = net_unpack(w)
+    ax = np.abs(x)
+    e1 = sum(np.abs(W1[:, m]).reshape((C, 1) + (1,) * (ax.ndim - 2)) * _ahead(ax, m - 2) for m in range(K))
     e2 = np.zeros_like(a1)
     for m in range(K):
-        e2 += np.tensordot(np.abs(W2[:, :, m]), _ahead(a1, m - 2), axes=(1, 0))
-    full = sum(np.tensordot(np.abs(W3[:, m]), _ahead(e2, m - 2), axes=(0, 0)) for m in range(K))
-    return u * full[::D]
+        e2 += np.tensordot(np.abs(W2[:, :, m]), _ahead(a1 + e1, m - 2), axes=(1, 0))
+    e3 = a2 + e2
+    full = sum(np.tensordot(np.abs(W3[:, m]), _ahead(e3, m - 2), axes=(0, 0)) for m in range(K))
+    return u * (1.0 + 4.0 * u) * full[::D]

@@ -52,14 +52,15 @@ constexpr int kMaxTapD = 128;      // largest decimation factor with a tap table
 constexpr int kNetChannels = 16, kNetTaps = 5;
 constexpr int kNetSize = kNetChannels * kNetTaps * (kNetChannels + 2);
 constexpr int kNetMaxD = 60;  // one output view per 64-view chunk needs D <= 60
-// Device copy of the learned decimation's weights, BF16-rounded: layer 2 as
-// the tensor-core B operands (tap m: 16 output x 16 input channels, K-major,
-// two 8-channel planes of 256 bytes), layers 1 and 3 as floats, plus the
-// plain low-pass taps h[|i|] it adds to.
+// Device copy of the learned decimation's weights, BF16-rounded, as the
+// tensor-core B operands (16 x 16, K-major, two 8-value planes of 256 bytes):
+// layer 2 per tap m (output x input channel), layer 1 (channel x tap, taps
+// past 5 zero), layer 3 (tap x channel, taps past 5 zero); plus the plain
+// low-pass taps h[|i|] the net's output adds to.  w2, b1, b3 are contiguous.
 struct __align__(16) NetWeights {
     uint16_t w2[kNetTaps * 256];
-    float w1[kNetChannels * kNetTaps];
-    float w3[kNetChannels * kNetTaps];
+    uint16_t b1[256];
+    uint16_t b3[256];
     float h[2 * kMaxTapD];
 };
 

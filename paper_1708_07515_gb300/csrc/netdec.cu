@@ -45,10 +45,11 @@ constexpr int kC = kNetChannels, kK = kNetTaps;
 constexpr int kG = 16;                 // shifted columns per CTA
 constexpr int kTileViews = 128 / kG;   // views per 128-row MMA tile
 constexpr int kTiles = 8;              // tiles per chunk
-constexpr int kKA = kTiles * kTileViews;   // a2 views per chunk
-constexpr int kNA1 = kKA + 4;          // a1 views per chunk (two each side)
-constexpr int kPlaneA1 = kNA1 * kG * 16;   // bytes of one K plane of a1
-constexpr int kNetThreads = 128;
+constexpr int kNA1 = kTiles * kTileViews;  // a1 views per chunk (a2 rows are computed for as many)
+constexpr int kKA = kNA1 - 4;          // a2 views per chunk with their whole support
+constexpr int kRowsA = kNA1 * kG + 64; // operand rows: the layer-2 taps read 64 rows past the tiles
+constexpr int kPlaneA1 = kRowsA * 16;  // bytes of one 8-channel plane
+constexpr int kNetThreads = 256;
 constexpr uint32_t kTmemCols = kTiles * 16;
 constexpr uint64_t kNetWaitNs = 2000000000ull;
 
@@ -78,6 +79,17 @@ __device__ __forceinline__ float shifted_sample(const TQ *__restrict__ Q, const 
     return fmaf(f, b - a, a);
 }
 
+// two floats -> BF16 pair (lo in the low half), negative values to 0
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *(const uint32_t *)&b;
+}
+
 struct NetChunk {
     int J;    // output views per chunk
     int XL;   // x views before the chunk's first output view
@@ -88,17 +100,33 @@ __host__ __device__ inline NetChunk net_chunk(int D, int HD) {
     NetChunk c;
     c.J = (kKA - 5) / D + 1;
     c.XL = HD - 1 > 6 ? HD - 1 : 6;
-    const int a = kNA1 + c.XL - 2, b = (c.J - 1) * D + HD + c.XL;
+    const int a = kNA1 + c.XL + 1, b = (c.J - 1) * D + HD + c.XL;
     c.NX = a > b ? a : b;
     return c;
 }
 
 // dynamic shared memory of net_decompose_kernel (bytes, after 128-byte alignment)
 __host__ __device__ inline size_t net_smem(const NetChunk &c, int HD) {
-    return 2 * (size_t)kPlaneA1 + sizeof(uint16_t) * kK * 256 + sizeof(float) * (size_t)c.NX * kG +
-           sizeof(float) * (size_t)c.J * kG + sizeof(float) * 2 * kC * kK + sizeof(float) * (size_t)HD;
+    return 2 * (size_t)kPlaneA1 + sizeof(uint16_t) * (kK + 2) * 256 + sizeof(float) * (size_t)c.NX * kG +
+           sizeof(float) * (size_t)c.J * kG + sizeof(float) * (size_t)HD;
 }
 
+// One CTA per (square q, detector row v, 16 shifted columns); the orbit is
+// walked in chunks of J output views.  Per chunk (operand rows are
+// (view, column) pairs, row = view * 16 + column; three rounds on the
+// tensor cores, M = 128 rows x N = 16 per tile, 8 tiles, FP32 in tensor
+// memory, BF16 operands in shared memory):
+//   1. x: the shifted samples of the chunk's views (FP32)
+//   2. layer-1 operand: row (view, column) = x at views view - 2 .. view + 5
+//      (BF16; taps 5..7 meet zero weights)
+//   3. z1 = one MMA per tile against W1 (K = 16 taps); meanwhile the plain
+//      low-pass of the chunk's output views (FP32, from x)
+//   4. a1 = relu(z1) as BF16, two 8-channel planes
+//   5. z2 = five MMAs per tile, tap m reading a1 from row 16 m on (K = 16 channels)
+//   6. a2 = relu(z2) as BF16, over a1
+//   7. p = one MMA per tile against W3 (N = its 5 taps, zero-padded)
+//   8. each row adds p[m] to the output view it feeds through tap m
+//   9. store
 template <typename TQ>
 __global__ void __launch_bounds__(kNetThreads, 4)
 net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const int32_t *__restrict__ crop,
@@ -125,21 +153,20 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
         return;
     }
     const NetChunk ch = net_chunk(D, HD);
-    unsigned char *a1 = base;                                       // 2 planes
-    unsigned char *w2 = a1 + 2 * kPlaneA1;                          // kK blocks of 512 bytes
-    float *xs = (float *)(w2 + sizeof(uint16_t) * kK * 256);        // [NX][kG]
+    unsigned char *opa = base;                                      // operands: 2 planes of kRowsA rows
+    unsigned char *wb = opa + 2 * kPlaneA1;                         // W2 (5 x 512 B), W1 (512 B), W3 (512 B)
+    float *xs = (float *)(wb + sizeof(uint16_t) * (kK + 2) * 256);  // [NX][kG]
     float *yacc = xs + (size_t)ch.NX * kG;                          // [J][kG]
-    float *w1s = yacc + (size_t)ch.J * kG;                          // [kC][kK]
-    float *w3s = w1s + kC * kK;                                     // [kC][kK]
-    float *hs = w3s + kC * kK;                                      // [HD]
+    float *hs = yacc + (size_t)ch.J * kG;                           // [HD]
 
-    for (int i = tid; i < kK * 256 / 8; i += kNetThreads)
-        ((uint4 *)w2)[i] = ((const uint4 *)net->w2)[i];
-    for (int i = tid; i < kC * kK; i += kNetThreads) {
-        w1s[i] = net->w1[i];
-        w3s[i] = net->w3[i];
-    }
+    for (int i = tid; i < (kK + 2) * 256 / 8; i += kNetThreads)
+        ((uint4 *)wb)[i] = ((const uint4 *)net->w2)[i];  // w2, b1, b3 are contiguous
     for (int i = tid; i < HD; i += kNetThreads) hs[i] = net->h[i];
+    // rows past the tiles: read by the tap offsets, must hold finite values
+    for (int i = tid; i < 2 * 64; i += kNetThreads) {
+        const int pl = i / 64, r = kNA1 * kG + i % 64;
+        *(uint4 *)(opa + (size_t)pl * kPlaneA1 + (size_t)r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
         tma::mbar_init(&bar, 1);
         tma::fence_mbar_init();
@@ -150,63 +177,82 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     tc5::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int warp = tid >> 5, lane = tid & 31;
-    const uint32_t sa1 = tma::smem_u32(a1), sw2 = tma::smem_u32(w2);
+    const int wq = warp & 3, wh = warp >> 2;  // tensor-memory lane quarter, half of the tiles
+    const uint32_t sopa = tma::smem_u32(opa), swb = tma::smem_u32(wb);
     constexpr uint32_t kIdesc = tc5::idesc_bf16_f32(128, 16);
+    // descriptors: operand planes (a1, a2: second plane kPlaneA1 on; the
+    // layer-1 operand has one plane, its second K half meets zero weights
+    // and is pointed 16 rows on), weights (two 256-byte planes)
+    const uint64_t dA12 = tc5::smem_desc(sopa, kPlaneA1, 128);
+    const uint64_t dX = tc5::smem_desc(sopa, 256, 128);
+    const uint64_t dW2 = tc5::smem_desc(swb, 256, 128);
+    const uint64_t dW1 = tc5::smem_desc(swb + kK * 512, 256, 128);
+    const uint64_t dW3 = tc5::smem_desc(swb + (kK + 1) * 512, 256, 128);
     const int nchunks = (Pd + ch.J - 1) / ch.J;
+    const int nfeed = 4 / D + 1;  // output views one a2 view can feed
+    const size_t qo = (size_t)q * P;
+    const TQ *Qv = Q + (size_t)v * Nu;  // row v of view 0
+    const size_t view_stride = (size_t)nrows * Nu;
+    uint32_t phase = 0;
     bool failed = false;
-    uint32_t fail_parity = 0;
 
-    for (int cc = 0; cc < nchunks; ++cc) {
-        const int j0 = cc * ch.J;
-        const int Jc = min(ch.J, Pd - j0);
-        const int kx0 = j0 * D - ch.XL;  // view of x[0]
-        // 1. shifted samples
-        for (int i = tid; i < ch.NX * kG; i += kNetThreads) {
-            const int ix = i / kG, g = i - ix * kG;
-            xs[i] = shifted_sample(Q, crop, geo, q, wrap(kx0 + ix, P), t0 + g, T, v, nrows, P, Nu);
-        }
-        __syncthreads();
-        // 2. layer 1: a1 view ka (= view j0 D - 4 + ka), column g, as BF16
-        {
-            const int g = tid & (kG - 1);
-            for (int ka = tid / kG; ka < kNA1; ka += kNetThreads / kG) {
-                const float *xp = xs + (size_t)(ka + ch.XL - 6) * kG + g;
-                const float x0 = xp[0], x1 = xp[kG], x2 = xp[2 * kG], x3 = xp[3 * kG], x4 = xp[4 * kG];
-                uint32_t pk[8];
-#pragma unroll
-                for (int c = 0; c < kC; c += 2) {
-                    const float *wa = w1s + c * kK, *wb = wa + kK;
-                    float za = wa[0] * x0, zb = wb[0] * x0;
-                    za = fmaf(wa[1], x1, za);
-                    zb = fmaf(wb[1], x1, zb);
-                    za = fmaf(wa[2], x2, za);
-                    zb = fmaf(wb[2], x2, zb);
-                    za = fmaf(wa[3], x3, za);
-                    zb = fmaf(wb[3], x3, zb);
-                    za = fmaf(wa[4], x4, za);
-                    zb = fmaf(wb[4], x4, zb);
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(za, 0.f), fmaxf(zb, 0.f));
-                    pk[c / 2] = *(const uint32_t *)&b2;
-                }
-                const int r = ka * kG + g;
-                *(uint4 *)(a1 + (size_t)r * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *(uint4 *)(a1 + kPlaneA1 + (size_t)r * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-        }
+    // wait for the MMAs committed last: one thread polls, the others sleep
+    // in the barrier; false on timeout (uniform)
+    auto mma_done = [&]() -> bool {
+        const bool ok = tid != 0 || tma::mbar_wait_bounded(&bar, phase, kNetWaitNs);
+        phase ^= 1u;
+        const bool all = __syncthreads_and(ok);
+        tc5::fence_after_sync();
+        return all;
+    };
+    // after writing an operand: visible to the tensor cores, tensor-memory
+    // reads of this thread ordered before the next MMA
+    auto operands_ready = [&]() {
         tma::fence_proxy_async();
         tc5::fence_before_sync();
         __syncthreads();
         tc5::fence_after_sync();
-        // 3. layer 2 on the tensor cores: tile i = a2 views 8i .. 8i + 7 of
-        // the chunk (rows view * 16 + column); tap m reads a1 from row 16 m on
+    };
+
+    for (int cc = 0; cc < nchunks && !failed; ++cc) {
+        const int j0 = cc * ch.J;
+        const int Jc = min(ch.J, Pd - j0);
+        const int kx0 = j0 * D - ch.XL;  // view of x[0]
+        // 1. shifted samples: one view per warp step, lanes 0..16 read the
+        // 17 crop columns t0 .. t0 + 16 (one coalesced segment), lane g
+        // interpolates between its sample and lane g + 1's
+#pragma unroll 3
+        for (int ix = warp; ix < ch.NX; ix += kNetThreads / 32) {
+            const int k = wrap(kx0 + ix, P);
+            const int c = __ldg(crop + qo + k) + t0 + lane;
+            const float f = __ldg(&geo[qo + k].frac);
+            const float a = (lane <= kG && c >= 0 && c < Nu) ? ld_q(Qv + (size_t)k * view_stride + c) : 0.f;
+            const float b = __shfl_down_sync(0xffffffffu, a, 1);
+            if (lane < kG) xs[ix * kG + lane] = (t0 + lane < T) ? fmaf(f, b - a, a) : 0.f;
+        }
+        __syncthreads();
+        // 2. layer-1 operand: a1 view ka (= view j0 D - 4 + ka) reads x at
+        // index ka + XL - 6 + t, t < 8; thread: column g, views 4 b .. 4 b + 3
+        {
+            const int g = tid & (kG - 1), b4 = (tid >> 4) * 4;
+            const float *xp = xs + (size_t)(b4 + ch.XL - 6) * kG + g;
+            float xw[11];
+#pragma unroll
+            for (int t = 0; t < 11; ++t) xw[t] = xp[t * kG];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = (b4 + i) * kG + g;
+                *(uint4 *)(opa + (size_t)r * 16) = make_uint4(bf16x2(xw[i], xw[i + 1]), bf16x2(xw[i + 2], xw[i + 3]),
+                                                               bf16x2(xw[i + 4], xw[i + 5]),
+                                                               bf16x2(xw[i + 6], xw[i + 7]));
+            }
+        }
+        operands_ready();
+        // 3. z1
         if (tid == 0) {
 #pragma unroll 1
             for (int i = 0; i < kTiles; ++i)
-#pragma unroll
-                for (int m = 0; m < kK; ++m)
-                    tc5::mma_bf16(tmem + (uint32_t)(16 * i),
-                                  tc5::smem_desc(sa1 + (uint32_t)((128 * i + 16 * m) * 16), kPlaneA1, 128),
-                                  tc5::smem_desc(sw2 + (uint32_t)(512 * m), 256, 128), kIdesc, m > 0 ? 1u : 0u);
+                tc5::mma_bf16(tmem + (uint32_t)(16 * i), dX + (uint64_t)(128 * i), dW1, kIdesc, 0u);
             tc5::commit(&bar);
         }
         // plain low-pass meanwhile: output view j0 + jl, column g
@@ -217,36 +263,74 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             for (int d = 1; d < HD; ++d) acc = fmaf(hs[d], xp[(size_t)d * kG] + xp[-(ptrdiff_t)d * kG], acc);
             yacc[i] = acc;
         }
-        __syncthreads();
-        const bool ok = tma::mbar_wait_bounded(&bar, (uint32_t)(cc & 1), kNetWaitNs);
-        if (!__syncthreads_and(ok)) {
+        if (!mma_done()) {
             failed = true;
-            fail_parity = (uint32_t)(cc & 1);
             break;
         }
-        tc5::fence_after_sync();
-        // 4. layer 3: row (view 8 i + 2 warp + lane / 16, column lane % 16)
+        // 4. and 6.: relu of tensor-memory rows -> BF16 operand planes; warp
+        // w reads lanes 32 (w % 4) .. + 31 of tiles 4 (w / 4) .. + 3
+        auto relu_to_operand = [&]() {
+#pragma unroll 1
+            for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
+                float z[16];
+                tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), z);
+                const int r = 128 * i + 32 * wq + lane;
+                *(uint4 *)(opa + (size_t)r * 16) = make_uint4(relu_bf16x2(z[0], z[1]), relu_bf16x2(z[2], z[3]),
+                                                              relu_bf16x2(z[4], z[5]), relu_bf16x2(z[6], z[7]));
+                *(uint4 *)(opa + kPlaneA1 + (size_t)r * 16) =
+                    make_uint4(relu_bf16x2(z[8], z[9]), relu_bf16x2(z[10], z[11]), relu_bf16x2(z[12], z[13]),
+                               relu_bf16x2(z[14], z[15]));
+            }
+        };
+        relu_to_operand();
+        operands_ready();
+        // 5. z2: tile i = a2 views 8 i .. 8 i + 7 (view ka2 = view j0 D - 2 +
+        // ka2); tap m reads a1 from row 16 m on
+        if (tid == 0) {
+#pragma unroll 1
+            for (int i = 0; i < kTiles; ++i)
+#pragma unroll
+                for (int m = 0; m < kK; ++m)
+                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i + 16 * m),
+                                  dW2 + (uint64_t)(32 * m), kIdesc, m > 0 ? 1u : 0u);
+            tc5::commit(&bar);
+        }
+        if (!mma_done()) {
+            failed = true;
+            break;
+        }
+        relu_to_operand();
+        operands_ready();
+        // 7. layer-3 terms p[row][m] = sum_c W3[c][m] a2[row][c]
+        if (tid == 0) {
+#pragma unroll 1
+            for (int i = 0; i < kTiles; ++i)
+                tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i), dW3, kIdesc, 0u);
+            tc5::commit(&bar);
+        }
+        if (!mma_done()) {
+            failed = true;
+            break;
+        }
+        // 8. a2 view ka2 feeds output view jl through tap m = ka2 - jl D
         {
             const int g = lane & (kG - 1);
 #pragma unroll 1
-            for (int i = 0; i < kTiles; ++i) {
-                float z[16];
-                tc5::ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * i), z);
-                const int ka2 = kTileViews * i + 2 * warp + (lane >> 4);
-                // output views jl with 0 <= ka2 - jl D <= 4
-                int jl = ka2 >= 4 ? (ka2 - 4 + D - 1) / D : 0;
-                for (; jl * D <= ka2 && jl < Jc; ++jl) {
-                    const float *w = w3s + (ka2 - jl * D);
-                    float p = 0.f;
-#pragma unroll
-                    for (int c = 0; c < kC; ++c) p = fmaf(w[c * kK], fmaxf(z[c], 0.f), p);
-                    atomicAdd(yacc + jl * kG + g, p);
+            for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
+                float pz[16];
+                tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), pz);
+                const int ka2 = kTileViews * i + 2 * wq + (lane >> 4);
+                const int jtop = ka2 / D;
+                for (int u = 0; u < nfeed; ++u) {
+                    const int jl = jtop - u, m = ka2 - jl * D;
+                    const float pm = m == 0 ? pz[0] : m == 1 ? pz[1] : m == 2 ? pz[2] : m == 3 ? pz[3] : pz[4];
+                    if (m <= 4 && jl >= 0 && jl < Jc && ka2 < kKA) atomicAdd(yacc + jl * kG + g, pm);
                 }
             }
         }
         tc5::fence_before_sync();
         __syncthreads();
-        // 5. store
+        // 9. store
         for (int i = tid; i < Jc * kG; i += kNetThreads) {
             const int jl = i / kG, t = t0 + (i - jl * kG);
             if (t < Tstride) outq[(size_t)(j0 + jl) * jstride + t] = yacc[i];
@@ -254,8 +338,10 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     }
     if (failed) {
         // the MMAs never signalled: report, give them another bounded wait, leave
-        if (tid == 0) atomicOr(status, 2);
-        tma::mbar_wait_bounded(&bar, fail_parity, kNetWaitNs);
+        if (tid == 0) {
+            atomicOr(status, 2);
+            tma::mbar_wait_bounded(&bar, phase ^ 1u, kNetWaitNs);
+        }
     }
     tc5::fence_before_sync();
     __syncthreads();
@@ -527,15 +613,16 @@ cudaError_t launch_net_decompose(const PlanImpl &p, const void *Q, float *out, c
 cudaError_t upload_net(PlanImpl &p) {
     NetWeights h{};
     const float *W1 = p.net_host, *W2 = p.net_host + kC * kK, *W3 = W2 + kC * kC * kK;
-    for (int i = 0; i < kC * kK; ++i) {
-        h.w1[i] = W1[i];
-        h.w3[i] = W3[i];
-    }
-    // tap m: B[n = c][k = c'] at byte (c' / 8) 256 + c 16 + (c' % 8) 2
-    for (int m = 0; m < kK; ++m)
+    // B operands, N x K = 16 x 16, K-major: element (n, k) at uint16 index
+    // (k / 8) 128 + n 8 + k % 8 (two 8-value planes of 256 bytes)
+    auto at = [](int n, int k) { return (k / 8) * 128 + n * 8 + (k % 8); };
+    for (int m = 0; m < kK; ++m)  // layer 2, tap m: n = output channel, k = input channel
         for (int c = 0; c < kC; ++c)
-            for (int ci = 0; ci < kC; ++ci)
-                h.w2[m * 256 + (ci / 8) * 128 + c * 8 + (ci % 8)] = bf16_bits(W2[(c * kC + ci) * kK + m]);
+            for (int ci = 0; ci < kC; ++ci) h.w2[m * 256 + at(c, ci)] = bf16_bits(W2[(c * kC + ci) * kK + m]);
+    for (int c = 0; c < kC; ++c)      // layer 1: n = channel, k = tap (taps 5..15 zero)
+        for (int m = 0; m < kK; ++m) h.b1[at(c, m)] = bf16_bits(W1[c * kK + m]);
+    for (int m = 0; m < kK; ++m)      // layer 3: n = tap (5..15 zero), k = channel
+        for (int c = 0; c < kC; ++c) h.b3[at(m, c)] = bf16_bits(W3[c * kK + m]);
     for (int i = 0; i < 2 * kMaxTapD; ++i) h.h[i] = (float)p.htaps[i];
     return cudaMemcpy(p.net, &h, sizeof(h), cudaMemcpyHostToDevice);
 }

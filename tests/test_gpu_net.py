@@ -3,17 +3,17 @@
 fdkod_backproject, and the training kernels (adjoint of the
 backprojection, backward pass of the net).
 
-Bars.  The kernel stores a1 (the tensor-core operand) as BF16, so it is
-compared with the oracle that rounds a1 to BF16 the same way: what remains
-is FP32 arithmetic and the rare a1 value whose FP32 and FP64 pre-images
-round to neighbouring BF16 values (a1 changes by one BF16 step there).
+Bars.  The kernel feeds every layer's input (x, a1, a2) to the tensor cores
+as BF16, so it is compared with the oracle that rounds the same values to
+BF16: what remains is FP32 arithmetic and the rare value whose FP32 and
+FP64 pre-images round to neighbouring BF16 values (one BF16 step there).
 Elementwise the difference must stay within the rigorous bound of one BF16
-rounding of every a1 (oracle.net.a1_rounding_bound) plus FP32 slack, and in
-norm within REL_NET of the data: an isolated one-step flip moves ~25
-outputs by ~2^-8 of their net term, so a few dozen flips among 10^5
-outputs stay well below it, while a wrong tap, channel or view index moves
-every output by the size of the net term.  The weights are BF16 values, so
-the kernel's BF16 weight storage is exact."""
+rounding of every such value (oracle.net.act_rounding_bound) plus FP32
+slack, and in norm within REL_NET of the data: an isolated one-step flip
+moves a few dozen outputs by ~2^-8 of their net term, so the flips among
+10^5 outputs stay well below it, while a wrong tap, channel or view index
+moves every output by the size of the net term.  The weights are BF16
+values, so the kernel's BF16 weight storage is exact."""
 import numpy as np
 import pytest
 
@@ -47,18 +47,27 @@ def _scan(oracle_mod, seed, N, Nu, Nv, P, R, n_ell=6):
     return oracle_mod.filter(p, R).astype(np.float32)
 
 
-def _cmp_decomposed(got, oracle_mod, Q, R, N, s, D, w, taps=None, what=""):
+def _cmp_decomposed(got, oracle_mod, Q, R, N, s, D, w, taps=None, what="", tight=True):
+    """tight: the norm bar REL_NET.  With 16-bit Q the shifted samples are
+    interpolations between 16-bit values and often land on a BF16 rounding
+    tie, where FP32 and FP64 decide differently far more often; the norm bar
+    is then the RMS of independent roundings, at most the bound's norm over
+    sqrt(3)."""
     Qo = Q.astype(np.float32)
     for q in range(4 ** s):
         T = int(oracle_mod.bounds(R, N, Q.shape[2], Q.shape[0], s)["T"][q])
-        want = oracle_mod.net_decomposed(Qo, R, N, s, D, q, w, taps, a1_round="bf16")
-        bound = onet.a1_rounding_bound(oracle_mod.shift_rows(Qo, R, N, s, q), D, w)
+        want = oracle_mod.net_decomposed(Qo, R, N, s, D, q, w, taps, act_round="bf16")
+        bound = onet.act_rounding_bound(oracle_mod.shift_rows(Qo, R, N, s, q), D, w)
         g = got[q, :, :, :T].astype(np.float64)
         err = np.abs(g - want)
         scale = np.abs(want).max()
         assert np.all(err <= bound + FP32_SLACK * scale), f"{what} q={q}: {(err - bound).max():.3e}"
-        rel = np.linalg.norm(g - want) / np.linalg.norm(want)
-        assert rel <= REL_NET, f"{what} q={q}: rel {rel:.3e}"
+        if tight:
+            rel = np.linalg.norm(g - want) / np.linalg.norm(want)
+            assert rel <= REL_NET, f"{what} q={q}: rel {rel:.3e}"
+        else:
+            assert np.linalg.norm(g - want) <= np.linalg.norm(bound) / np.sqrt(3.0) + \
+                FP32_SLACK * np.linalg.norm(want), what
         assert np.all(got[q, :, :, T:] == 0.0)
 
 
@@ -84,7 +93,7 @@ def test_net_decompose_matches_oracle(fd, oracle_mod, N, Nu, Nv, P, s, D, taps, 
         got = plan.decompose(Qp).cpu().numpy()
         assert plan.device_status() == 0
     Qref = Qp.float().cpu().numpy()   # the values the kernel read (16-bit storage rounds Q)
-    _cmp_decomposed(got, oracle_mod, Qref, R, N, s, D, w, taps=h, what=f"{qtype} D={D}")
+    _cmp_decomposed(got, oracle_mod, Qref, R, N, s, D, w, taps=h, what=f"{qtype} D={D}", tight=qtype == "f32")
 
 
 def test_linear_net_configuration_equals_plain_taps(fd, oracle_mod):
@@ -106,7 +115,7 @@ def test_linear_net_configuration_equals_plain_taps(fd, oracle_mod):
         b = pt.decompose(Qd).cpu().numpy().astype(np.float64)
     bn = 0.0
     for q in range(4):
-        bound = onet.a1_rounding_bound(oracle_mod.shift_rows(Q, R, N, s, q), D, w)
+        bound = onet.act_rounding_bound(oracle_mod.shift_rows(Q, R, N, s, q), D, w)
         T = bound.shape[-1]
         assert np.all(np.abs(a[q, :, :, :T] - b[q, :, :, :T]) <= bound + FP32_SLACK * np.abs(b).max())
         bn += np.sum(bound ** 2)
@@ -144,7 +153,7 @@ def test_net_backprojection_matches_oracle(fd, oracle_mod):
         plan.set_net(w)
         vol = plan.backproject(torch.from_numpy(Q).cuda()).cpu().numpy()
         assert plan.device_status() == 0
-    want = oracle_mod.fdkod_net_slices(Q, R, N, s, D, w, zs, a1_round="bf16")
+    want = oracle_mod.fdkod_net_slices(Q, R, N, s, D, w, zs, act_round="bf16")
     got = vol[zs].astype(np.float64)
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert rel <= REL_NET, rel
@@ -164,8 +173,10 @@ def test_net_slab_pipeline_uses_the_net(fd, oracle_mod):
         Q = plan.filter(torch.from_numpy(proj).cuda())
         whole = plan.backproject(Q).cpu().numpy()
         slabs = fd.reconstruct_slabs(plan, proj, 8)
-    # per-slab filtering pairs rows differently in the FFT: FP32 round-off only
-    assert np.linalg.norm(slabs - whole) / np.linalg.norm(whole) <= 1e-5
+    # per-slab filtering pairs rows differently in the FFT: FP32 round-off of
+    # Q, which now and then moves a net input across a BF16 rounding
+    # boundary (one BF16 step of one value there, as in the oracle bars)
+    assert np.linalg.norm(slabs - whole) / np.linalg.norm(whole) <= REL_NET
 
 
 # ---------------------------------------------------------------- training

@@ -204,10 +204,12 @@ def test_round_bf16_matches_the_format():
     assert np.all(f == np.round(f))
 
 
-def test_a1_rounding_bound_covers_bf16_storage():
+def test_act_rounding_bound_covers_bf16_storage():
     rng = np.random.default_rng(51)
-    x = rng.standard_normal((48, 30))
-    w = _rand_net(52)
-    d = np.abs(net.net_forward(x, 4, w, a1_round="bf16") - net.net_forward(x, 4, w))
-    assert np.all(d <= net.a1_rounding_bound(x, 4, w))
-    assert d.max() > 0
+    for D in (2, 4, 7):
+        x = rng.standard_normal((56, 30)) * 10.0 ** rng.uniform(-2, 2)
+        w = _rand_net(52 + D)
+        d = np.abs(net.net_forward(x, D, w, act_round="bf16") - net.net_forward(x, D, w))
+        b = net.act_rounding_bound(x, D, w)
+        assert np.all(d <= b)
+        assert d.max() > 0
