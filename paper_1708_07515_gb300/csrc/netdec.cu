@@ -107,35 +107,55 @@ __host__ __device__ inline NetChunk net_chunk(int D, int HD) {
 
 // dynamic shared memory of net_decompose_kernel (bytes, after 128-byte alignment)
 __host__ __device__ inline size_t net_smem(const NetChunk &c, int HD) {
-    return 2 * (size_t)kPlaneA1 + sizeof(uint16_t) * (kK + 2) * 256 + sizeof(float) * (size_t)c.NX * kG +
+    return 2 * (size_t)kPlaneA1 + sizeof(uint16_t) * (kK + 2) * 256 + 2 * sizeof(float) * (size_t)c.NX * kG +
            sizeof(float) * (size_t)c.J * kG + sizeof(float) * (size_t)HD;
 }
 
+// barrier 1: the consumer warps only (the producers run ahead)
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kNetThreads) : "memory"); }
+__device__ __forceinline__ bool consumers_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kNetThreads)
+        : "memory");
+    return r != 0;
+}
+
 // One CTA per (square q, detector row v, 16 shifted columns); the orbit is
-// walked in chunks of J output views.  Per chunk (operand rows are
+// walked in chunks of J output views.  Two producer warps interpolate the
+// shifted samples x of the next chunk into the other half of a
+// double-buffered tile (mbarriers full / empty) while eight consumer warps
+// work on the current one.  Per chunk the consumers run (operand rows are
 // (view, column) pairs, row = view * 16 + column; three rounds on the
 // tensor cores, M = 128 rows x N = 16 per tile, 8 tiles, FP32 in tensor
 // memory, BF16 operands in shared memory):
-//   1. x: the shifted samples of the chunk's views (FP32)
-//   2. layer-1 operand: row (view, column) = x at views view - 2 .. view + 5
+//   1. layer-1 operand: row (view, column) = x at views view - 2 .. view + 5
 //      (BF16; taps 5..7 meet zero weights)
-//   3. z1 = one MMA per tile against W1 (K = 16 taps); meanwhile the plain
+//   2. z1 = one MMA per tile against W1 (K = 16 taps); meanwhile the plain
 //      low-pass of the chunk's output views (FP32, from x)
-//   4. a1 = relu(z1) as BF16, two 8-channel planes
-//   5. z2 = five MMAs per tile, tap m reading a1 from row 16 m on (K = 16 channels)
-//   6. a2 = relu(z2) as BF16, over a1
-//   7. p = one MMA per tile against W3 (N = its 5 taps, zero-padded)
-//   8. each row adds p[m] to the output view it feeds through tap m
-//   9. store
+//   3. a1 = relu(z1) as BF16, two 8-channel planes
+//   4. z2 = five MMAs per tile, tap m reading a1 from row 16 m on (K = 16 channels)
+//   5. a2 = relu(z2) as BF16, over a1
+//   6. p = one MMA per tile against W3 (N = its 5 taps, zero-padded)
+//   7. each row adds p[m] to the output view it feeds through tap m
+//   8. store
+constexpr int kProducerWarps = 2;
+constexpr int kNetCtaThreads = kNetThreads + 32 * kProducerWarps;
+
 template <typename TQ>
-__global__ void __launch_bounds__(kNetThreads, 4)
+__global__ void __launch_bounds__(kNetCtaThreads, 4)
 net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const int32_t *__restrict__ crop,
                      const GeomEntry *__restrict__ geo, const int32_t *__restrict__ Tq,
                      const NetWeights *__restrict__ net, int *status, int Tstride, int P, int D, int Pd, int HD,
                      int nrows, int Nu, int ngroups) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, full[2], empty[2];
     __shared__ uint32_t tmem_slot;
 
     const int q = blockIdx.x / ngroups, grp = blockIdx.x - q * ngroups;
@@ -146,7 +166,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     float *outq = out + ((size_t)q * Pd * nrows + v) * Tstride;
     const int tid = threadIdx.x;
     if (t0 >= T) {  // past this square's row length: zeros (uniform per CTA)
-        for (int i = tid; i < Pd * kG; i += kNetThreads) {
+        for (int i = tid; i < Pd * kG; i += kNetCtaThreads) {
             const int j = i / kG, t = t0 + i % kG;
             if (t < Tstride) outq[(size_t)j * jstride + t] = 0.f;
         }
@@ -155,20 +175,24 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     const NetChunk ch = net_chunk(D, HD);
     unsigned char *opa = base;                                      // operands: 2 planes of kRowsA rows
     unsigned char *wb = opa + 2 * kPlaneA1;                         // W2 (5 x 512 B), W1 (512 B), W3 (512 B)
-    float *xs = (float *)(wb + sizeof(uint16_t) * (kK + 2) * 256);  // [NX][kG]
-    float *yacc = xs + (size_t)ch.NX * kG;                          // [J][kG]
+    float *xbuf = (float *)(wb + sizeof(uint16_t) * (kK + 2) * 256);  // 2 x [NX][kG]
+    float *yacc = xbuf + 2 * (size_t)ch.NX * kG;                    // [J][kG]
     float *hs = yacc + (size_t)ch.J * kG;                           // [HD]
 
-    for (int i = tid; i < (kK + 2) * 256 / 8; i += kNetThreads)
+    for (int i = tid; i < (kK + 2) * 256 / 8; i += kNetCtaThreads)
         ((uint4 *)wb)[i] = ((const uint4 *)net->w2)[i];  // w2, b1, b3 are contiguous
-    for (int i = tid; i < HD; i += kNetThreads) hs[i] = net->h[i];
+    for (int i = tid; i < HD; i += kNetCtaThreads) hs[i] = net->h[i];
     // rows past the tiles: read by the tap offsets, must hold finite values
-    for (int i = tid; i < 2 * 64; i += kNetThreads) {
+    for (int i = tid; i < 2 * 64; i += kNetCtaThreads) {
         const int pl = i / 64, r = kNA1 * kG + i % 64;
         *(uint4 *)(opa + (size_t)pl * kPlaneA1 + (size_t)r * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid == 0) {
         tma::mbar_init(&bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            tma::mbar_init(&full[b], 32 * kProducerWarps);
+            tma::mbar_init(&empty[b], kNetThreads);
+        }
         tma::fence_mbar_init();
     }
     if (tid < 32) tc5::alloc(&tmem_slot, kTmemCols);
@@ -177,98 +201,74 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     tc5::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int warp = tid >> 5, lane = tid & 31;
-    const int wq = warp & 3, wh = warp >> 2;  // tensor-memory lane quarter, half of the tiles
-    const uint32_t sopa = tma::smem_u32(opa), swb = tma::smem_u32(wb);
-    constexpr uint32_t kIdesc = tc5::idesc_bf16_f32(128, 16);
-    // descriptors: operand planes (a1, a2: second plane kPlaneA1 on; the
-    // layer-1 operand has one plane, its second K half meets zero weights
-    // and is pointed 16 rows on), weights (two 256-byte planes)
-    const uint64_t dA12 = tc5::smem_desc(sopa, kPlaneA1, 128);
-    const uint64_t dX = tc5::smem_desc(sopa, 256, 128);
-    const uint64_t dW2 = tc5::smem_desc(swb, 256, 128);
-    const uint64_t dW1 = tc5::smem_desc(swb + kK * 512, 256, 128);
-    const uint64_t dW3 = tc5::smem_desc(swb + (kK + 1) * 512, 256, 128);
     const int nchunks = (Pd + ch.J - 1) / ch.J;
-    const int nfeed = 4 / D + 1;  // output views one a2 view can feed
-    const size_t qo = (size_t)q * P;
-    const TQ *Qv = Q + (size_t)v * Nu;  // row v of view 0
-    const size_t view_stride = (size_t)nrows * Nu;
-    uint32_t phase = 0;
-    bool failed = false;
 
-    // wait for the MMAs committed last: one thread polls, the others sleep
-    // in the barrier; false on timeout (uniform)
-    auto mma_done = [&]() -> bool {
-        const bool ok = tid != 0 || tma::mbar_wait_bounded(&bar, phase, kNetWaitNs);
-        phase ^= 1u;
-        const bool all = __syncthreads_and(ok);
-        tc5::fence_after_sync();
-        return all;
-    };
-    // after writing an operand: visible to the tensor cores, tensor-memory
-    // reads of this thread ordered before the next MMA
-    auto operands_ready = [&]() {
-        tma::fence_proxy_async();
-        tc5::fence_before_sync();
-        __syncthreads();
-        tc5::fence_after_sync();
-    };
-
-    for (int cc = 0; cc < nchunks && !failed; ++cc) {
-        const int j0 = cc * ch.J;
-        const int Jc = min(ch.J, Pd - j0);
-        const int kx0 = j0 * D - ch.XL;  // view of x[0]
-        // 1. shifted samples: one view per warp step, lanes 0..16 read the
-        // 17 crop columns t0 .. t0 + 16 (one coalesced segment), lane g
-        // interpolates between its sample and lane g + 1's
-#pragma unroll 3
-        for (int ix = warp; ix < ch.NX; ix += kNetThreads / 32) {
-            const int k = wrap(kx0 + ix, P);
-            const int c = __ldg(crop + qo + k) + t0 + lane;
-            const float f = __ldg(&geo[qo + k].frac);
-            const float a = (lane <= kG && c >= 0 && c < Nu) ? ld_q(Qv + (size_t)k * view_stride + c) : 0.f;
-            const float b = __shfl_down_sync(0xffffffffu, a, 1);
-            if (lane < kG) xs[ix * kG + lane] = (t0 + lane < T) ? fmaf(f, b - a, a) : 0.f;
-        }
-        __syncthreads();
-        // 2. layer-1 operand: a1 view ka (= view j0 D - 4 + ka) reads x at
-        // index ka + XL - 6 + t, t < 8; thread: column g, views 4 b .. 4 b + 3
-        {
-            const int g = tid & (kG - 1), b4 = (tid >> 4) * 4;
-            const float *xp = xs + (size_t)(b4 + ch.XL - 6) * kG + g;
-            float xw[11];
-#pragma unroll
-            for (int t = 0; t < 11; ++t) xw[t] = xp[t * kG];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = (b4 + i) * kG + g;
-                *(uint4 *)(opa + (size_t)r * 16) = make_uint4(bf16x2(xw[i], xw[i + 1]), bf16x2(xw[i + 2], xw[i + 3]),
-                                                               bf16x2(xw[i + 4], xw[i + 5]),
-                                                               bf16x2(xw[i + 6], xw[i + 7]));
+    if (warp >= kNetThreads / 32) {
+        // ---- producers: x of chunk cc into buffer cc % 2; thread pt covers
+        // column g = pt % 16 of views pt / 16, + 4, + 8, ...
+        const int pt = tid - kNetThreads, g = pt & (kG - 1);
+        const size_t qo = (size_t)q * P;
+        const TQ *Qv = Q + (size_t)v * Nu;
+        const size_t view_stride = (size_t)nrows * Nu;
+        const bool col_in = t0 + g < T;
+        for (int cc = 0; cc < nchunks; ++cc) {
+            const int b = cc & 1;
+            if (cc >= 2 && !tma::mbar_wait_bounded(&empty[b], (uint32_t)(((cc >> 1) - 1) & 1), kNetWaitNs)) {
+                atomicOr(status, 2);
+                break;
             }
+            float *xs = xbuf + (size_t)b * ch.NX * kG;
+            int k = cc * ch.J * D - ch.XL + (pt >> 4);
+            if (k < 0 || k >= P) k = wrap(k, P);
+#pragma unroll 8
+            for (int ix = pt >> 4; ix < ch.NX; ix += 32 * kProducerWarps / kG) {
+                const size_t o = qo + k;
+                const int c = __ldg(crop + o) + t0 + g;
+                const float f = __ldg(&geo[o].frac);
+                const TQ *r = Qv + (size_t)k * view_stride;
+                const float a = (col_in && c >= 0 && c < Nu) ? ld_q(r + c) : 0.f;
+                const float bb = (col_in && c + 1 >= 0 && c + 1 < Nu) ? ld_q(r + c + 1) : 0.f;
+                xs[ix * kG + g] = fmaf(f, bb - a, a);
+                k += 32 * kProducerWarps / kG;
+                if (k >= P) k = wrap(k, P);
+            }
+            tma::mbar_arrive(&full[b]);
         }
-        operands_ready();
-        // 3. z1
-        if (tid == 0) {
-#pragma unroll 1
-            for (int i = 0; i < kTiles; ++i)
-                tc5::mma_bf16(tmem + (uint32_t)(16 * i), dX + (uint64_t)(128 * i), dW1, kIdesc, 0u);
-            tc5::commit(&bar);
-        }
-        // plain low-pass meanwhile: output view j0 + jl, column g
-        for (int i = tid; i < Jc * kG; i += kNetThreads) {
-            const int jl = i / kG, g = i - jl * kG;
-            const float *xp = xs + (size_t)(jl * D + ch.XL) * kG + g;
-            float acc = hs[0] * xp[0];
-            for (int d = 1; d < HD; ++d) acc = fmaf(hs[d], xp[(size_t)d * kG] + xp[-(ptrdiff_t)d * kG], acc);
-            yacc[i] = acc;
-        }
-        if (!mma_done()) {
-            failed = true;
-            break;
-        }
-        // 4. and 6.: relu of tensor-memory rows -> BF16 operand planes; warp
-        // w reads lanes 32 (w % 4) .. + 31 of tiles 4 (w / 4) .. + 3
+    } else {
+        // ---- consumers
+        const int wq = warp & 3, wh = warp >> 2;  // tensor-memory lane quarter, half of the tiles
+        const uint32_t sopa = tma::smem_u32(opa), swb = tma::smem_u32(wb);
+        constexpr uint32_t kIdesc = tc5::idesc_bf16_f32(128, 16);
+        // descriptors: operand planes (a1, a2: second plane kPlaneA1 on; the
+        // layer-1 operand has one plane, its second K half meets zero weights
+        // and is pointed 16 rows on), weights (two 256-byte planes)
+        const uint64_t dA12 = tc5::smem_desc(sopa, kPlaneA1, 128);
+        const uint64_t dX = tc5::smem_desc(sopa, 256, 128);
+        const uint64_t dW2 = tc5::smem_desc(swb, 256, 128);
+        const uint64_t dW1 = tc5::smem_desc(swb + kK * 512, 256, 128);
+        const uint64_t dW3 = tc5::smem_desc(swb + (kK + 1) * 512, 256, 128);
+        uint32_t phase = 0;
+        bool failed = false;
+
+        // wait for the MMAs committed last: one thread polls, the others
+        // sleep in the barrier; false on timeout (uniform)
+        auto mma_done = [&]() -> bool {
+            const bool ok = tid != 0 || tma::mbar_wait_spin(&bar, phase, kNetWaitNs);
+            phase ^= 1u;
+            const bool all = consumers_and(ok);
+            tc5::fence_after_sync();
+            return all;
+        };
+        // after writing an operand: visible to the tensor cores, tensor-memory
+        // reads of this thread ordered before the next MMA
+        auto operands_ready = [&]() {
+            tma::fence_proxy_async();
+            tc5::fence_before_sync();
+            consumers_sync();
+            tc5::fence_after_sync();
+        };
+        // relu of tensor-memory rows -> BF16 operand planes; warp w reads
+        // lanes 32 (w % 4) .. + 31 of tiles 4 (w / 4) .. + 3
         auto relu_to_operand = [&]() {
 #pragma unroll 1
             for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
@@ -282,63 +282,117 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
                                relu_bf16x2(z[14], z[15]));
             }
         };
-        relu_to_operand();
-        operands_ready();
-        // 5. z2: tile i = a2 views 8 i .. 8 i + 7 (view ka2 = view j0 D - 2 +
-        // ka2); tap m reads a1 from row 16 m on
-        if (tid == 0) {
+
+        for (int cc = 0; cc < nchunks && !failed; ++cc) {
+            const int j0 = cc * ch.J;
+            const int Jc = min(ch.J, Pd - j0);
+            const int b = cc & 1;
+            const float *xs = xbuf + (size_t)b * ch.NX * kG;
+            const bool xok = tid != 0 || tma::mbar_wait_spin(&full[b], (uint32_t)((cc >> 1) & 1), kNetWaitNs);
+            if (!consumers_and(xok)) {
+                failed = true;
+                break;
+            }
+            // 1. layer-1 operand: a1 view ka (= view j0 D - 4 + ka) reads x at
+            // index ka + XL - 6 + t, t < 8; thread: column g, views 4 b .. 4 b + 3
+            {
+                const int g = tid & (kG - 1), b4 = (tid >> 4) * 4;
+                const float *xp = xs + (size_t)(b4 + ch.XL - 6) * kG + g;
+                float xw[11];
+#pragma unroll
+                for (int t = 0; t < 11; ++t) xw[t] = xp[t * kG];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = (b4 + i) * kG + g;
+                    *(uint4 *)(opa + (size_t)r * 16) =
+                        make_uint4(bf16x2(xw[i], xw[i + 1]), bf16x2(xw[i + 2], xw[i + 3]),
+                                   bf16x2(xw[i + 4], xw[i + 5]), bf16x2(xw[i + 6], xw[i + 7]));
+                }
+            }
+            operands_ready();
+            // 2. z1
+            if (tid == 0) {
 #pragma unroll 1
-            for (int i = 0; i < kTiles; ++i)
+                for (int i = 0; i < kTiles; ++i)
+                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dX + (uint64_t)(128 * i), dW1, kIdesc, 0u);
+                tc5::commit(&bar);
+            }
+            // plain low-pass meanwhile: output view j0 + jl, column g; then x
+            // is no longer needed: hand the buffer back to the producers
+            for (int i = tid; i < Jc * kG; i += kNetThreads) {
+                const int jl = i / kG, g = i - jl * kG;
+                const float *xp = xs + (size_t)(jl * D + ch.XL) * kG + g;
+                float acc = hs[0] * xp[0];
+                for (int d = 1; d < HD; ++d) acc = fmaf(hs[d], xp[(size_t)d * kG] + xp[-(ptrdiff_t)d * kG], acc);
+                yacc[i] = acc;
+            }
+            tma::mbar_arrive(&empty[b]);
+            if (!mma_done()) {
+                failed = true;
+                break;
+            }
+            // 3. a1
+            relu_to_operand();
+            operands_ready();
+            // 4. z2: tile i = a2 views 8 i .. 8 i + 7 (view ka2 = view j0 D - 2
+            // + ka2); tap m reads a1 from row 16 m on
+            if (tid == 0) {
+                // tap-major order: consecutive MMAs write different tiles
 #pragma unroll
                 for (int m = 0; m < kK; ++m)
-                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i + 16 * m),
-                                  dW2 + (uint64_t)(32 * m), kIdesc, m > 0 ? 1u : 0u);
-            tc5::commit(&bar);
-        }
-        if (!mma_done()) {
-            failed = true;
-            break;
-        }
-        relu_to_operand();
-        operands_ready();
-        // 7. layer-3 terms p[row][m] = sum_c W3[c][m] a2[row][c]
-        if (tid == 0) {
 #pragma unroll 1
-            for (int i = 0; i < kTiles; ++i)
-                tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i), dW3, kIdesc, 0u);
-            tc5::commit(&bar);
-        }
-        if (!mma_done()) {
-            failed = true;
-            break;
-        }
-        // 8. a2 view ka2 feeds output view jl through tap m = ka2 - jl D
-        {
-            const int g = lane & (kG - 1);
+                    for (int i = 0; i < kTiles; ++i)
+                        tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i + 16 * m),
+                                      dW2 + (uint64_t)(32 * m), kIdesc, m > 0 ? 1u : 0u);
+                tc5::commit(&bar);
+            }
+            if (!mma_done()) {
+                failed = true;
+                break;
+            }
+            // 5. a2
+            relu_to_operand();
+            operands_ready();
+            // 6. layer-3 terms p[row][m] = sum_c W3[c][m] a2[row][c]
+            if (tid == 0) {
+#pragma unroll 1
+                for (int i = 0; i < kTiles; ++i)
+                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i), dW3, kIdesc, 0u);
+                tc5::commit(&bar);
+            }
+            if (!mma_done()) {
+                failed = true;
+                break;
+            }
+            // 7. the layer-3 terms of every row to shared memory (over a2,
+            // whose MMAs are done): pm[ka2][m][g], m < 5
+            float *pm = (float *)opa;
 #pragma unroll 1
             for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
                 float pz[16];
                 tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), pz);
-                const int ka2 = kTileViews * i + 2 * wq + (lane >> 4);
-                const int jtop = ka2 / D;
-                for (int u = 0; u < nfeed; ++u) {
-                    const int jl = jtop - u, m = ka2 - jl * D;
-                    const float pm = m == 0 ? pz[0] : m == 1 ? pz[1] : m == 2 ? pz[2] : m == 3 ? pz[3] : pz[4];
-                    if (m <= 4 && jl >= 0 && jl < Jc && ka2 < kKA) atomicAdd(yacc + jl * kG + g, pm);
-                }
+                const int ka2 = kTileViews * i + 2 * wq + (lane >> 4), g = lane & (kG - 1);
+                float *dst = pm + (size_t)ka2 * kK * kG + g;
+#pragma unroll
+                for (int m = 0; m < kK; ++m) dst[m * kG] = pz[m];
             }
+            tc5::fence_before_sync();
+            consumers_sync();
+            // 8. output view j0 + jl = plain low-pass + sum_m pm[jl D + m][m]
+            for (int i = tid; i < Jc * kG; i += kNetThreads) {
+                const int jl = i / kG, g = i - jl * kG, t = t0 + g;
+                const float *src = pm + (size_t)jl * D * kK * kG + g;
+                float y = yacc[i];
+#pragma unroll
+                for (int m = 0; m < kK; ++m) y += src[(size_t)(m * kK + m) * kG];
+                if (t < Tstride) outq[(size_t)(j0 + jl) * jstride + t] = y;
+            }
+            // (the next chunk writes its layer-1 operand over pm only after
+            // the barrier of its x wait)
         }
-        tc5::fence_before_sync();
-        __syncthreads();
-        // 9. store
-        for (int i = tid; i < Jc * kG; i += kNetThreads) {
-            const int jl = i / kG, t = t0 + (i - jl * kG);
-            if (t < Tstride) outq[(size_t)(j0 + jl) * jstride + t] = yacc[i];
-        }
-    }
-    if (failed) {
-        // the MMAs never signalled: report, give them another bounded wait, leave
-        if (tid == 0) {
+        if (failed && tid == 0) {
+            // a wait gave up: report; if MMAs are in flight, give them
+            // another bounded wait before tensor memory is freed
             atomicOr(status, 2);
             tma::mbar_wait_bounded(&bar, phase ^ 1u, kNetWaitNs);
         }
@@ -358,7 +412,7 @@ cudaError_t launch_net_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_
     if (e != cudaSuccess) return e;
     const int ngroups = (p.Tstride + kG - 1) / kG;
     dim3 grid((unsigned)(ngroups * p.od.nsq), (unsigned)nrows);
-    net_decompose_kernel<TQ><<<grid, kNetThreads, smem, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.net, p.status,
+    net_decompose_kernel<TQ><<<grid, kNetCtaThreads, smem, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.net, p.status,
                                                              p.Tstride, p.g.P, p.D, p.Pd, HD, nrows, p.g.Nu,
                                                              ngroups);
     return cudaGetLastError();
