@@ -582,11 +582,21 @@ def main():
         Qo.reshape(-1, w.Nu)[flat] = oracle.filter_rows(proj, w.R, flat)
         ref_fdk = oracle.fdk_slices(Qo, w.R, w.N, zs)
         if net_w is not None:
-            ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, act_round="bf16")
+            # the net's oracle runs numpy per square: all squares up to 512^3,
+            # 16 seeded squares beyond (their voxels only)
+            nsq = 4 ** w.s
+            squares = None if nsq <= 64 else sorted(np.random.default_rng(w.seed).choice(nsq, 16, replace=False))
+            ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, act_round="bf16",
+                                             squares=squares)
         else:
+            squares = None
             ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
                                          taps=None if args.taps == "triangle" else plan.taps)
         g = vol_od[zs].astype(np.float64)
+        if squares is not None:
+            mask = oracle.square_mask(w.N, w.s, squares)[None]
+            g, ref_fdk = g * mask, ref_fdk * mask
+            extra["accuracy_squares"] = [int(q) for q in squares]
         extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(g - ref_od) / np.linalg.norm(ref_od))
         extra["rel_rmse_vs_fp64_fdk_oracle"] = float(np.linalg.norm(g - ref_fdk) / np.linalg.norm(ref_fdk))
         extra["accuracy_slices"] = zs

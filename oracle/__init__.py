@@ -328,13 +328,23 @@ def net_decomposed(Q: np.ndarray, R: float, N: int, s: int, D: int, q: int, w, t
 
 
 def fdkod_net_slices(Q: np.ndarray, R: float, N: int, s: int, D: int, w, zs, taps=None,
-                     act_round=None) -> np.ndarray:
+                     act_round=None, squares=None) -> np.ndarray:
     """FDK-OD slices with the learned decimation (D > 1); only the detector
-    rows the slices touch are decomposed."""
+    rows the slices touch are decomposed.  squares: compute only these
+    squares' voxels (the others stay 0), for sampled checks at large N."""
     P, Nv, Nu = np.shape(Q)
     zs = np.asarray(zs).reshape(-1)
     rows = slice_rows(R, N, Nv, zs)
     vol = np.zeros((zs.size, N, N))
-    for q in range(4 ** s):
+    for q in (range(4 ** s) if squares is None else squares):
         vol += bp_square(net_decomposed(Q, R, N, s, D, q, w, taps, act_round, rows), R, N, Nu, P, s, D, q, zs)
     return vol
+
+
+def square_mask(N: int, s: int, squares) -> np.ndarray:
+    """[N][N] boolean mask (y, x) of the voxels of the given squares (voxel i
+    belongs to square floor(i 2^s / N))."""
+    m = 1 << s
+    sq = (np.arange(N) * m) // N
+    q = sq[:, None] * m + sq[None, :]
+    return np.isin(q, np.asarray(list(squares)))

@@ -8,7 +8,7 @@ for one training scan (filtered projections Q on the device) and a batch of
 slices:
 
   1. S' = the decomposition with the current weights (the tensor-core
-     inference kernel: BF16 weights, BF16 a1, FP32 accumulation);
+     inference kernel: BF16 weights and layer inputs, FP32 accumulation);
   2. f = the FDK-OD backprojection of S';
   3. per slice z, fdkod_net_adjoint turns e = f[z] - f_FDK[z] into dS, the
      gradient of (1/2) sum e^2 with respect to S';
@@ -42,6 +42,67 @@ def init_weights(seed: int) -> np.ndarray:
     w1 = rng.standard_normal(80) * np.sqrt(2.0 / 5.0)
     w2 = rng.standard_normal(1280) * np.sqrt(2.0 / 80.0)
     return np.concatenate([w1, w2, np.zeros(80)]).astype(np.float32)
+
+
+def linear_config(g: dict, seed: int, scale: float = 0.05) -> np.ndarray:
+    """Weights under which the net adds the linear FIR sum_o g[o] x[jD + o]
+    (|o| <= 6) to the plain low-pass: channel pairs carry relu(+x) and
+    relu(-x) shifted by -4, 0 and +4 views through layers 1 and 2 (relu(u)
+    - relu(-u) = u), and layer 3 reads their differences at offsets -6..-3,
+    -2..2 and 3..6.  The other 10 channels of layers 1 and 2 get small
+    random weights (their layer-3 weights start at zero)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((16, 5)) * scale
+    W2 = rng.standard_normal((16, 16, 5)) * scale
+    W3 = np.zeros((16, 5))
+    W1[:6] = 0.0
+    W2[:6] = 0.0
+    for p, (shift, offs) in enumerate([(-4, range(-6, -2)), (0, range(-2, 3)), (4, range(3, 7))]):
+        cp, cn = 2 * p, 2 * p + 1
+        o1 = shift // 2                      # split the shift over layers 1 and 2
+        o2 = shift - o1
+        W1[cp, o1 + 2], W1[cn, o1 + 2] = 1.0, -1.0
+        W2[cp, cp, o2 + 2], W2[cp, cn, o2 + 2] = 1.0, -1.0
+        W2[cn, cn, o2 + 2], W2[cn, cp, o2 + 2] = 1.0, -1.0
+        for o in offs:
+            m = o - shift + 2
+            W3[cp, m], W3[cn, m] = g.get(o, 0.0), -g.get(o, 0.0)
+    return np.concatenate([W1.reshape(-1), W2.reshape(-1), W3.reshape(-1)]).astype(np.float32)
+
+
+def linear_fit(R: float, N: int, P: int, s: int, D: int, projs, zs, half: int = 6) -> dict:
+    """The symmetric FIR correction g[o] = g[-o], |o| <= half, that, added to
+    the plain triangle (whose support |i| < D may reach past it), brings
+    FDK-OD closest to full FDK on the training scans, with zero gain at zero
+    frequency (the total keeps unit gain).  With B_i the reconstruction from
+    the unit tap pair at +-i (library kernels, learn.normal_equations):
+    minimise |sum_i (tri_i + g_i) B_i - f_FDK|^2 subject to c . g = 0,
+    c = (1, 2, 2, ...), a KKT system of half + 2 unknowns.  Returns
+    {offset: g}."""
+    from . import learn
+    from .fdkod import Plan
+    n = half + 1
+    H = 2 if max(n, D) > D else 1            # tap blocks: cover |i| <= half and the triangle
+    if max(n, D) > 2 * D:
+        raise ValueError("the fit's plan takes at most 2 D taps")
+    m = H * D
+    G = np.zeros((m, m))
+    b = np.zeros(m)
+    with Plan(R, N, N, N, P, s, D) as pt, Plan(R, N, N, N, P, s, 1) as pf:
+        for proj in projs:
+            Q = pt.filter(proj)
+            gg, bb, _, _ = learn.normal_equations(pt, pf, Q, m, zs)
+            G += gg
+            b += bb
+    tri = np.maximum(D - np.arange(m), 0) / float(D * D)
+    c = learn.constraint(n)
+    K = np.zeros((n + 1, n + 1))
+    K[:n, :n] = G[:n, :n]
+    K[:n, n] = c
+    K[n, :n] = c
+    rhs = np.concatenate([b[:n] - G[:n] @ tri, [0.0]])
+    g = np.linalg.solve(K, rhs)[:n]
+    return {o: float(g[abs(o)]) for o in range(-half, half + 1)}
 
 
 class Adam:
@@ -133,19 +194,30 @@ class Trainer:
         return (num / den) ** 0.5
 
 
-def train(tr: Trainer, steps: int, lr: float, slices: int, seed: int, w0=None, log_every: int = 10):
+def train(tr: Trainer, steps: int, lr: float, slices: int, seed: int, w0=None, log_every: int = 10,
+          val_slices=None):
+    """Adam with a linear warm-up (a tenth of the steps) and a cosine-decayed
+    step size.  The curve holds (step, loss of
+    that step's slices) and, with val_slices, the rel-RMSE on those fixed
+    slices of every training scan (the step's own loss depends on which
+    slices it drew)."""
     rng = np.random.default_rng(seed)
     w = init_weights(seed) if w0 is None else np.asarray(w0, np.float32)
     opt = Adam(NET_SIZE, lr)
     N = tr.N
     curve = []
+    warm = max(1, steps // 10)
     for it in range(steps):
+        opt.lr = lr * min(1.0, (it + 1) / warm) * 0.5 * (1.0 + np.cos(np.pi * it / steps))
         scan = it % len(tr.scans)
         zs = rng.integers(N // 10, N - N // 10, size=slices)
         loss, g = tr.loss_and_grad(w, scan, zs)
         w = opt.step(w, g)
         if it % log_every == 0 or it == steps - 1:
-            curve.append((it, loss))
+            entry = [it, loss]
+            if val_slices is not None:
+                entry.append(tr.rel_rmse(w, tr.scans, val_slices))
+            curve.append(tuple(entry))
     return w, curve
 
 
@@ -169,6 +241,11 @@ def main(argv=None):
     ap.add_argument("--eval-slices", type=int, default=16)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--out", default=None, help="write the trained weights here (.npy)")
+    ap.add_argument("--log-every", type=int, default=25)
+    ap.add_argument("--linear", action="store_true", help="also fit the linear learned FIR (learn.py)")
+    ap.add_argument("--init", choices=["linear", "random"], default="linear",
+                    help="start at the best linear FIR within the net's reach (13 taps) or at random layers 1-2 "
+                         "with a zero layer 3")
     args = ap.parse_args(argv)
     N, P, s, D = args.N, args.P, args.s, args.D
     R = 4.0 * N
@@ -177,28 +254,43 @@ def main(argv=None):
     def scan(seed):
         return phantom.project_gpu(phantom.make_phantom(seed, N, args.ellipsoids), R, N, N, P)
 
+    zs = np.linspace(N // 8, N - 1 - N // 8, args.eval_slices).round().astype(int)
     tr = Trainer(R, N, P, s, D)
     try:
-        for i in range(args.train):
-            tr.add_scan(scan(8000 + i))
+        projs = [scan(8000 + i) for i in range(args.train)]
+        for p in projs:
+            tr.add_scan(p)
         t0 = time.time()
-        w, curve = train(tr, args.steps, args.lr, args.slices, args.seed)
+        w0 = None
+        if args.init == "linear":
+            g = linear_fit(R, N, P, s, D, projs, zs)
+            w0 = linear_config(g, args.seed)
+            init_err = tr.rel_rmse(w0, tr.scans, zs[::4])
+        w, curve = train(tr, args.steps, args.lr, args.slices, args.seed, w0=w0, log_every=args.log_every,
+                         val_slices=zs[::4])
         t_train = time.time() - t0
         held = []
         for i in range(args.test):
             tr.add_scan(scan(9000 + i))
             held.append(tr.scans.pop())
-        zs = np.linspace(N // 8, N - 1 - N // 8, args.eval_slices).round().astype(int)
         errs = {"triangle": tr.rel_rmse(None, held, zs), "net": tr.rel_rmse(w, held, zs)}
+        if w0 is not None:
+            errs["net_at_init"] = tr.rel_rmse(w0, held, zs)
         tr.plan.set_taps(fdkod_sinc_taps(D, 2))
         errs["sinc"] = tr.rel_rmse(None, held, zs)
+        if args.linear:
+            # the linear learned FIR (learn.py) fitted on the same training scans
+            from . import learn
+            h = learn.learn(R, N, P, s, D, 2, projs, zs)
+            tr.plan.set_taps(h)
+            errs["learned_linear"] = tr.rel_rmse(None, held, zs)
     finally:
         tr.close()
     if args.out:
         np.save(args.out, w)
     print(json.dumps({"N": N, "P": P, "s": s, "D": D, "steps": args.steps, "train_scans": args.train,
                       "held_out_scans": args.test, "train_seconds": round(t_train, 2),
-                      "loss_curve": [(i, float(f"{l:.4e}")) for i, l in curve],
+                      "curve": [[int(c[0])] + [float(f"{x:.5e}") for x in c[1:]] for c in curve],
                       "rel_rmse_vs_fdk": errs}))
 
 

@@ -38,7 +38,7 @@ def test_training_reduces_the_error_against_full_fdk(fd):
         held_net = tr.rel_rmse(w, held, zs_eval)
     finally:
         tr.close()
-    losses = np.array([l for _, l in curve])
+    losses = np.array([c[1] for c in curve])
     assert np.isfinite(losses).all()
     assert losses[-10:].mean() < 0.9 * losses[:3].mean(), losses
     assert after < before, (before, after)

@@ -52,3 +52,18 @@ def test_learned_taps_are_best_on_their_training_scans():
     assert errs["learned"] <= errs["triangle"] * (1 + 1e-6)
     assert errs["learned"] <= errs["sinc"] * (1 + 1e-6)
     assert abs(learn.constraint(H * D) @ h - 1.0) < 1e-9
+
+
+def test_net_linear_configuration_is_the_fir():
+    """learn_net.linear_config: the net (evaluated by the oracle) adds
+    exactly the 13-tap FIR it was given, at every output view."""
+    from oracle import net as onet
+
+    from paper_1708_07515_gb300.learn_net import linear_config
+    rng = np.random.default_rng(70)
+    g = {o: float(rng.standard_normal()) for o in range(-6, 7)}
+    w = linear_config(g, 3).astype(np.float64)
+    for P, D in ((48, 4), (60, 3), (64, 16)):
+        x = rng.standard_normal((P, 5))
+        want = sum(c * np.roll(x, -o, axis=0) for o, c in g.items())[::D]
+        np.testing.assert_allclose(onet.net_forward(x, D, w), want, rtol=0, atol=1e-5 * np.abs(want).max())
