@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--batched", action="store_true",
                     help="64 volumes of uneven size (N in {64..384}, P = 1.4 N) in one CUDA graph")
+    ap.add_argument("--persistent", action="store_true",
+                    help="batched form: all volumes' backprojections in one persistent launch (after every "
+                         "decomposition) instead of one launch per volume on its stream")
     ap.add_argument("--slabs", type=int, default=0,
                     help="slab-wise (piecemeal, Sec. 2.2) reconstruction from host buffers, this many slices per slab")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
@@ -297,7 +300,7 @@ def batched_main(args):
     insts = [Instance(R, N, N, N, P) for N, P, R, _ in work]
     projs = [phantom.project_gpu(phantom.make_phantom(sd, N, 20), R, N, N, P) for N, P, R, sd in work]
     rates = autotune.measure_rates()
-    br = BatchReconstructor(insts, rates=rates)
+    br = BatchReconstructor(insts, rates=rates, persistent=args.persistent)
     br.load(projs)
     br.capture()
     for _ in range(args.warmup):
@@ -318,7 +321,7 @@ def batched_main(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (projections generated on the GPU)",
            "config": {"workload": "batched_64_volumes_N64-384_P1.4N", "volumes": len(insts),
                       "step": "one CUDA-graph launch: bounds + filter + decompose + backproject of every volume",
-                      "streams": len(br.lanes),
+                      "streams": len(br.lanes), "persistent_backprojection": br.batch is not None,
                       "choices": [[i.N, i.P, i.s, i.D] for i in insts], "rates": list(rates)},
            "gpu_launches": br.launches() * args.steps, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)

@@ -155,9 +155,10 @@ int fdk_backproject_plain(fdkod_plan_t *plan, const void *Q, float *vol, uintptr
  * The decomposition stage on its own (Sec. 2.1 shift + angular
  * decimation): writes S'[q][j][v][t] (float32, t < T_stride, zero for
  * t >= T[q]) for all squares q, decimated views j < P/D and rows v to the
- * device buffer out of info.decomposed_elems floats.  For inspection and
- * tests; fdkod_backproject uses the plan's own workspace.  Errors:
- * INVALID_ARG (also when D == 1), CUDA.
+ * device buffer out of info.decomposed_elems floats, or, with out NULL, to
+ * the plan's own workspace (the one fdkod_backproject uses; the batched
+ * backprojection reads it).  Errors: INVALID_ARG (also when D == 1, or out
+ * NULL for a plan without a workspace), CUDA.
  */
 int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t stream);
 
@@ -365,6 +366,32 @@ int fdkod_net_adjoint(fdkod_plan_t *plan, const float *vol_slice, const float *r
                       float *sq_err, uintptr_t stream);
 int fdkod_net_backward(fdkod_plan_t *plan, const void *Q, const float *w, const float *dS, int row_lo,
                        int row_hi, float *dW, uintptr_t stream);
+
+/*
+ * Batched backprojection (the batched form): many plans' FDK-OD
+ * backprojections in one persistent launch.  fdkod_batch_create records, per
+ * plan i, its source src[i] (device; D = 1: Q, float32 [P][Nv][Nu]; D > 1:
+ * decomposed data [4^s][P/D][Nv][T_stride] as fdkod_decompose writes it, or
+ * NULL for the plan's own workspace, which fdkod_decompose fills when its
+ * out is NULL) and volume vols[i] (device, [N][N][N]); it builds one tensor
+ * map per plan and a work list of (plan, tile, z-slab) items, largest plans
+ * first, on the device (synchronous; the batch keeps pointers, not copies:
+ * the plans and buffers must outlive it).  fdkod_batch_backproject resets
+ * the work counter and launches one kernel of as many CTAs as the GPU
+ * holds; each takes items until none are left (asynchronous on `stream`,
+ * no allocation: it can be captured into a CUDA graph).  The result equals
+ * each plan's fdkod_backproject_decomposed / fdkod_backproject of the same
+ * source.  Device-side status (window overflow, wait timeout) goes to each
+ * plan's status word (fdkod_last_device_status).  Errors: INVALID_ARG (null
+ * pointers, count < 1, NULL source for a plan without one), UNSUPPORTED (a
+ * plan with 16-bit Q and D = 1, or windows that no TMA box holds: use the
+ * per-plan entry points), OOM, CUDA.
+ */
+typedef struct fdkod_batch fdkod_batch_t;
+int fdkod_batch_create(fdkod_plan_t *const *plans, const void *const *src, float *const *vols, int count,
+                       fdkod_batch_t **out);
+int fdkod_batch_backproject(fdkod_batch_t *batch, uintptr_t stream);
+void fdkod_batch_destroy(fdkod_batch_t *batch);
 
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);

@@ -10,6 +10,7 @@ from .fdkod import (  # noqa: F401
     FDKOD_F16,
     FDKOD_F32,
     FDKOD_NET_SIZE,
+    BatchBackprojection,
     FdkodError,
     Plan,
     fdk_backproject_plain,

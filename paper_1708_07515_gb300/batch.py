@@ -1,21 +1,28 @@
 """Many reconstructions of uneven size in one CUDA graph.
 
 Each volume gets its own plan (s and D chosen by the autotuner from the
-Eq. 4-6 cost model with this GPU's measured rates), its own device buffers,
-and the four stages of the hot path (bounds, filter, decomposition,
-backprojection) for every volume are captured once into a single CUDA graph;
-a batch then runs as one graph launch.  Volumes are independent, so they are
-spread over several streams (largest estimated cost first, each to the
-least-loaded stream): in the graph they become parallel branches and small
-volumes fill the SMs that a large one leaves idle.  All kernels are
-libfdkod's; torch only provides memory, streams and the graph object.
+Eq. 4-6 cost model with this GPU's measured rates) and its own device
+buffers.  The bounds, filter and decomposition of every volume are spread
+over several streams (largest estimated cost first, each to the
+least-loaded stream; in the graph they become parallel branches), each
+followed on its stream by the volume's backprojection, so one volume's
+filter and decomposition overlap other volumes' backprojections.  With
+persistent=True the backprojections of all volumes -- most of the work --
+are instead one persistent launch after every decomposition
+(fdkod_batch_backproject: a work list of (volume, tile, z-slab) items,
+largest volumes first, taken by as many CTAs as the GPU holds); it gives
+the same volumes bit for bit but gives up that overlap (a kernel cannot
+wait for another launch's results), which costs more than it saves (207
+against 187 ms for 64 volumes of N 64-384).  The whole batch is captured
+once into a single CUDA graph and runs as one graph launch.  All kernels
+are libfdkod's; torch only provides memory, streams and the graph object.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass
 
 from . import autotune
-from .fdkod import Plan
+from .fdkod import BatchBackprojection, FdkodError, Plan
 
 
 def work_estimate(inst) -> float:
@@ -48,7 +55,7 @@ class Instance:
 
 class BatchReconstructor:
     def __init__(self, instances: list[Instance], qtype: str = "f32", rates: tuple[float, float] | None = None,
-                 skip: int = 0, streams: int = 4):
+                 skip: int = 0, streams: int = 4, persistent: bool = False):
         import torch
         self.torch = torch
         self.instances = instances
@@ -69,24 +76,39 @@ class BatchReconstructor:
         self.stream = torch.cuda.Stream()
         self.lanes = [torch.cuda.Stream() for _ in range(max(1, streams))]
         self.assign = assign_lanes([work_estimate(i) for i in instances], len(self.lanes))
+        self.batch = None
+        if persistent:
+            try:
+                self.batch = BatchBackprojection(self.plans, [Q if i.D == 1 else None for i, Q in
+                                                              zip(instances, self.Q)], self.vol)
+            except FdkodError as e:
+                if e.status != -2:
+                    raise
 
     def launches(self) -> int:
-        """Kernel launches per batch: bounds, filter, and the decomposition
-        (only when D > 1) plus the backprojection of every volume."""
-        return sum(4 if i.D > 1 else 3 for i in self.instances)
+        """Kernel launches per batch: bounds, filter and the decomposition
+        (only when D > 1) of every volume, plus one persistent
+        backprojection (or one backprojection per volume)."""
+        per = sum(3 if i.D > 1 else 2 for i in self.instances)
+        return per + (1 if self.batch is not None else len(self.instances))
 
     def _enqueue(self, main):
         """Every volume's stages on its lane; the lanes fork from and join
         back into `main` (in a capture they become parallel graph branches)."""
         for lane in self.lanes:
             lane.wait_stream(main)
-        for k, (plan, p, Q, v) in enumerate(zip(self.plans, self.proj, self.Q, self.vol)):
+        for k, (inst, plan, p, Q, v) in enumerate(zip(self.instances, self.plans, self.proj, self.Q, self.vol)):
             h = int(self.lanes[self.assign[k]].cuda_stream)
             plan.compute_bounds(h)
             plan.filter(p, Q, h)
-            plan.backproject(Q, v, h)
+            if self.batch is None:
+                plan.backproject(Q, v, h)
+            elif inst.D > 1:
+                plan.decompose_to_workspace(Q, h)
         for lane in self.lanes:
             main.wait_stream(lane)
+        if self.batch is not None:
+            self.batch.run(int(main.cuda_stream))
 
     def run_eager(self):
         """All stages launched one by one (forked over the lanes from the
@@ -117,6 +139,9 @@ class BatchReconstructor:
             dst.copy_(self.torch.as_tensor(src), non_blocking=True)
 
     def close(self):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
         for p in self.plans:
             p.close()
         self.plans = []

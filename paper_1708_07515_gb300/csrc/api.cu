@@ -388,7 +388,9 @@ int fdk_backproject_plain(fdkod_plan_t *plan, const void *Q, float *vol, uintptr
 }
 
 int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t stream) {
-    if (!plan || !Q || !out || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    if (!plan || !Q || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    if (!out) out = plan->impl.Sp;  // the plan's own workspace
+    if (!out) return FDKOD_ERR_INVALID_ARG;
     return cuda_status(launch_decompose(plan->impl, Q, out, (cudaStream_t)stream));
 }
 
@@ -531,3 +533,40 @@ const char *fdkod_strerror(int status) {
 }
 
 }  // extern "C"
+
+struct fdkod_batch {
+    fdkod::BatchImpl *impl = nullptr;
+};
+
+int fdkod_batch_create(fdkod_plan_t *const *plans, const void *const *src, float *const *vols, int count,
+                       fdkod_batch_t **out) {
+    if (!plans || !vols || !out || count < 1) return FDKOD_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<const fdkod::PlanImpl *> p((size_t)count);
+    std::vector<const void *> s((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !vols[i]) return FDKOD_ERR_INVALID_ARG;
+        p[i] = &plans[i]->impl;
+        s[i] = src ? src[i] : nullptr;
+        if (!s[i]) s[i] = p[i]->D > 1 ? (const void *)p[i]->Sp : nullptr;  // the plan's workspace
+        if (!s[i]) return FDKOD_ERR_INVALID_ARG;
+    }
+    bool supported = false;
+    fdkod::BatchImpl *b = nullptr;
+    const cudaError_t e = fdkod::batch_create(p.data(), s.data(), vols, count, &b, supported);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!supported || !b) return FDKOD_ERR_UNSUPPORTED;
+    *out = new fdkod_batch{b};
+    return FDKOD_OK;
+}
+
+int fdkod_batch_backproject(fdkod_batch_t *batch, uintptr_t stream) {
+    if (!batch || !batch->impl) return FDKOD_ERR_INVALID_ARG;
+    return cuda_status(fdkod::batch_launch(*batch->impl, (cudaStream_t)stream));
+}
+
+void fdkod_batch_destroy(fdkod_batch_t *batch) {
+    if (!batch) return;
+    fdkod::batch_destroy(batch->impl);
+    delete batch;
+}

@@ -25,6 +25,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "fdkod_internal.cuh"
 #include "tma.cuh"
@@ -535,6 +537,195 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form for a batch of plans (float32 windows): one launch, as
+// many CTAs as fit the GPU, each taking work items (plan, tile, z-slab) from
+// an atomic counter until the list is exhausted; per item the arithmetic of
+// bp_tma_kernel, with the plan's tensor map and parameters read from global
+// memory and the window width a run-time value (the second window row is one
+// add away).  The mbarrier stages continue from item to item.
+struct BatchInst {
+    BpTmaParams a;
+    int direct, WD;
+};
+
+__global__ void __launch_bounds__(kThreads, 3)
+bp_persistent_kernel(const CUtensorMap *__restrict__ maps, const BatchInst *__restrict__ insts,
+                     const int4 *__restrict__ items, int nitems, int *counter) {
+    constexpr int kAl = 4;  // float windows: 16-byte copy alignment in elements
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *sm = (float *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    const uint32_t sbase = tma::smem_u32(sm);
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ float4 s_pa[2][kViewsPerStage];
+    __shared__ float4 s_pb[2][kViewsPerStage];
+    __shared__ float s_zcr[2][kViewsPerStage];
+    __shared__ int s_tx[2][kViewsPerStage], s_ty[2][kViewsPerStage], s_tz[2][kViewsPerStage];
+    __shared__ int s_skip[2][kViewsPerStage];
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
+        tma::fence_mbar_init();
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t gc = 0;  // chunks this CTA has run: stage gc % 2, parity (gc / 2) % 2
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int4 it = items[item];  // plan, tile, z-slab
+        const BpTmaParams a = insts[it.x].a;
+        const bool direct = insts[it.x].direct != 0;
+        const int WD = insts[it.x].WD;
+        const CUtensorMap *map = maps + it.x;
+
+        const int tiles = a.tps * a.tps;
+        const int q = it.y / tiles;
+        const int tt = it.y - q * tiles;
+        const int qy = q / a.m, qx = q - qy * a.m;
+        int ix0, ix1, iy0, iy1;
+        square_range(qx, a.m, a.N, ix0, ix1);
+        square_range(qy, a.m, a.N, iy0, iy1);
+        const int x0 = ix0 + (tt % a.tps) * kTile;
+        const int y0 = iy0 + (tt / a.tps) * kTile;
+        if (x0 > ix1 || y0 > iy1) continue;  // ragged square: empty tile (uniform)
+        const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
+        const int z0 = a.zoff + it.z * kZT;
+        const int z1 = min(z0 + kZT - 1, a.zoff + a.nz - 1);
+        const float half_n = 0.5f * (float)(a.N - 1);
+        const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;
+        const float yc = 0.5f * ((float)iy0 + (float)iy1) - half_n;
+        const float zc = (float)z0 + 0.5f * (float)(kZT - 1) - half_n;
+        const float vcd = 0.5f * (float)(a.Nv - 1);
+        const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+        const int x = x0 + lx, y = y0 + ly;
+        const bool active = x <= xe && y <= ye;
+        const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
+        const int32_t w0q = a.w0[q];
+        const int nch = (a.nviews + kViewsPerStage - 1) / kViewsPerStage;
+
+        auto setup = [&](int c, int st) {
+            const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+            if (warp < nj) {
+                const int j = c * kViewsPerStage + warp;
+                const int k = j * a.vstep;
+                const size_t o = (size_t)q * a.P + k;
+                const GeomEntry ge = a.geo[o];
+                const int cbase = direct ? a.crop[o] : 0;
+                const float toff = direct ? ge.frac - (float)w0q : -(float)w0q;
+                const int cc = lane & 7;
+                const float cx = (float)((cc & 1) ? xe : x0) - half_n - xc;
+                const float cy = (float)((cc & 2) ? ye : y0) - half_n - yc;
+                const float cz = (cc & 4) ? 0.5f * (float)(kZT - 1) : -0.5f * (float)(kZT - 1);
+                const float dd = fmaf(ge.cb, cx, ge.sb * cy);
+                const float invU = __fdividef(ge.g_hi, fmaf(ge.r, dd, 1.0f));
+                const float t = fmaf(invU, fmaf(ge.alpha, cx, ge.gamma * cy), toff);
+                const float zcr = zc * ge.r;
+                const float ph = zc * ge.g_hi;
+                const float pl = fmaf(zc, ge.g_lo, fmaf(zc, ge.g_hi, -ph));
+                const float v = (ph + vcd) + (pl + invU * (cz - zcr * dd));
+                float tmin = t, tmax = t, vmin = v, vmax = v;
+#pragma unroll
+                for (int off = 4; off > 0; off >>= 1) {
+                    tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
+                    tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+                    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+                }
+                if (lane == 0) {
+                    const int clo = cbase + (int)floorf(tmin) - 1;
+                    const int chi = cbase + (int)floorf(tmax) + 2;
+                    const int xs = clo & ~(kAl - 1);
+                    const int vlo = (int)floorf(vmin) - 1;
+                    const int vhi = (int)floorf(vmax) + 2;
+                    const int skip = (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1);
+                    if (skip) atomicOr(a.status, 1);
+                    s_pa[st][warp] = make_float4(ge.cb, ge.sb, ge.r, ge.alpha);
+                    s_pb[st][warp] = make_float4(ge.gamma, ge.g_hi, toff - (float)(xs - cbase),
+                                                 (ph - ((float)vlo - vcd)) + pl);
+                    s_zcr[st][warp] = zcr;
+                    s_tx[st][warp] = xs;
+                    s_ty[st][warp] = vlo - a.row0;
+                    s_tz[st][warp] = direct ? k : q * a.Pd + j;
+                    s_skip[st][warp] = skip;
+                }
+            }
+        };
+        auto issue = [&](int c, int st) {
+            const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+            tma::fence_proxy_async();
+            tma::mbar_arrive_expect_tx(&bars[st], (uint32_t)(nj * a.RW * WD * 4));
+            for (int w = 0; w < nj; ++w)
+                tma::load_3d(sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride, map, &bars[st], s_tx[st][w],
+                             s_ty[st][w], s_tz[st][w]);
+        };
+
+        setup(0, (int)(gc & 1u));
+        __syncthreads();
+        if (threadIdx.x == 0) issue(0, (int)(gc & 1u));
+        float acc[kZT];
+#pragma unroll
+        for (int i = 0; i < kZT; ++i) acc[i] = 0.f;
+        const uint32_t rowb = 4u * (uint32_t)WD;
+        for (int c = 0; c < nch; ++c) {
+            const uint32_t g = gc + (uint32_t)c;
+            const int st = (int)(g & 1u);
+            if (c + 1 < nch) setup(c + 1, st ^ 1);
+            __syncthreads();
+            if (c + 1 < nch && threadIdx.x == 0) issue(c + 1, st ^ 1);
+            const bool ok = tma::mbar_wait_bounded(&bars[st], (g >> 1) & 1u, kWaitLimitNs);
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) atomicOr(a.status, 2);
+                tma::mbar_wait_bounded(&bars[st], (g >> 1) & 1u, kWaitLimitNs);
+                if (c + 1 < nch) tma::mbar_wait_bounded(&bars[st ^ 1], ((g + 1) >> 1) & 1u, kWaitLimitNs);
+                return;
+            }
+            if (active) {
+                const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
+                for (int w = 0; w < nj; ++w) {
+                    if (s_skip[st][w]) continue;
+                    const float4 pa = s_pa[st][w];
+                    const float4 pb = s_pb[st][w];
+                    const float dd = fmaf(pa.x, dx, pa.y * dy);
+                    const float invU = __fdividef(pb.y, fmaf(pa.z, dd, 1.0f));
+                    const float t = fmaf(invU, fmaf(pa.w, dx, pb.x * dy), pb.z);
+                    const float tf = floorf(t);
+                    const float wgt = invU * invU;
+                    const float a1 = wgt * (t - tf);
+                    const float a0 = wgt - a1;
+                    const float vb0 = fmaf(invU, -0.5f * (float)(kZT - 1) - s_zcr[st][w] * dd, pb.w);
+                    const uint32_t tbase = sbase + 4u * ((uint32_t)(st * kViewsPerStage + w) *
+                                                             (uint32_t)a.tile_stride + (uint32_t)(int)tf) -
+                                           (uint32_t)kMagicBits * rowb;
+#pragma unroll
+                    for (int i = 0; i < kZT; ++i) {
+                        const float v = fmaf(invU, (float)i, vb0);
+                        const float fl = floorf(v);
+                        const float fv = v - fl;
+                        const uint32_t ad = (uint32_t)((int)fl + kMagicBits) * rowb + tbase;
+                        const uint32_t ad2 = ad + rowb;
+                        const float c0 = fmaf(a1, Lds<float, 4>::f(ad), a0 * Lds<float, 0>::f(ad));
+                        const float c1 = fmaf(a1, Lds<float, 4>::f(ad2), a0 * Lds<float, 0>::f(ad2));
+                        acc[i] = fmaf(fv, c1 - c0, acc[i] + c0);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        gc += (uint32_t)nch;
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < kZT; ++i)
+                if (z0 + i <= z1) a.vol[((size_t)(z0 + i - a.zoff) * a.N + y) * a.N + x] = acc[i] * a.scale;
+        }
+    }
+}
+
 template <typename TS, bool DIRECT, int WD>
 cudaError_t launch_tma_t(const CUtensorMap &map, const BpTmaParams &prm, int nsq, cudaStream_t st) {
     const size_t smem = sizeof(TS) * (size_t)2 * kViewsPerStage * prm.tile_stride + 128;
@@ -560,14 +751,14 @@ cudaError_t launch_tma_w(int WD, const CUtensorMap &map, const BpTmaParams &prm,
 // The TMA path applies when the source is 16-byte aligned, its rows are whole
 // 16-byte units, and the window fits a box (<= 256 rows, width an
 // instantiated WD).  The decomposed data is float32; Q may be 16-bit.
-cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
-                           cudaStream_t st, const Band &b, bool &launched) {
-    launched = false;
+// Fills the tensor map, the parameters and the window width; false when the
+// TMA path does not apply.
+bool make_tma_launch(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
+                     const Band &b, CUtensorMap &map, BpTmaParams &a, int &WD) {
     const int es = (direct && p.qtype != FDKOD_F32) ? 2 : 4;
-    const int WD = es == 4 ? ss.WdT : ss.WdT16;
-    if (WD == 0 || ss.Rw > 256 || ((uintptr_t)src & 15) != 0) return cudaSuccess;
-    if (direct && ((size_t)p.g.Nu * es) % 16 != 0) return cudaSuccess;
-    CUtensorMap map;
+    WD = es == 4 ? ss.WdT : ss.WdT16;
+    if (WD == 0 || ss.Rw > 256 || ((uintptr_t)src & 15) != 0) return false;
+    if (direct && ((size_t)p.g.Nu * es) % 16 != 0) return false;
     uint64_t dims[3], strides[2];
     if (direct) {
         dims[0] = (uint64_t)p.g.Nu;
@@ -585,9 +776,8 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
     const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (p.qtype == FDKOD_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-    cudaError_t e = encode_map_3d(&map, dt, src, dims, strides, box);
-    if (e != cudaSuccess) return cudaSuccess;  // not encodable: generic path
-    BpTmaParams a{};
+    if (encode_map_3d(&map, dt, src, dims, strides, box) != cudaSuccess) return false;  // generic path
+    a = BpTmaParams{};
     a.vol = vol;
     a.geo = ss.geo;
     a.crop = ss.crop;
@@ -614,6 +804,16 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
         a.vstep = p.D;
         a.scale = (float)(M_PI / (double)p.Pd);
     }
+    return true;
+}
+
+cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
+                           cudaStream_t st, const Band &b, bool &launched) {
+    launched = false;
+    CUtensorMap map;
+    BpTmaParams a;
+    int WD = 0;
+    if (!make_tma_launch(p, ss, direct, src, vol, b, map, a, WD)) return cudaSuccess;
     launched = true;
     if (!direct) return launch_tma_w<float, false>(WD, map, a, ss.nsq, st);
     switch (p.qtype) {
@@ -677,6 +877,100 @@ cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool dire
     a.vstep = p.D;
     a.scale = (float)(M_PI / (double)p.Pd);
     return launch_t<float, false>(a, ss.nsq, st);
+}
+
+// ---- batch of plans, one persistent launch --------------------------------
+
+struct BatchImpl {
+    CUtensorMap *maps = nullptr;
+    BatchInst *insts = nullptr;
+    int4 *items = nullptr;
+    int *counter = nullptr;
+    int nitems = 0;
+    size_t smem = 0;
+    int grid = 0;
+};
+
+namespace {
+void batch_free_impl(BatchImpl *b) {
+    cudaFree(b->maps);
+    cudaFree(b->insts);
+    cudaFree(b->items);
+    cudaFree(b->counter);
+    delete b;
+}
+}  // namespace
+
+cudaError_t batch_create(const PlanImpl *const *plans, const void *const *src, float *const *vols, int count,
+                         BatchImpl **out, bool &supported) {
+    supported = false;
+    *out = nullptr;
+    std::vector<CUtensorMap> maps((size_t)count);
+    std::vector<BatchInst> insts((size_t)count);
+    std::vector<std::pair<double, int>> order;
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        const PlanImpl &p = *plans[i];
+        const bool direct = p.D == 1;
+        if (direct && p.qtype != FDKOD_F32) return cudaSuccess;  // 16-bit windows: not in the batch form
+        Band b;
+        b.nrows = p.g.Nv;
+        b.nz = p.g.N;
+        int WD = 0;
+        if (!make_tma_launch(p, p.od, direct, src[i], vols[i], b, maps[i], insts[i].a, WD)) return cudaSuccess;
+        insts[i].direct = direct ? 1 : 0;
+        insts[i].WD = WD;
+        smem = std::max(smem, sizeof(float) * (size_t)2 * kViewsPerStage * insts[i].a.tile_stride + 128);
+        order.push_back({-(double)p.g.N * p.g.N * p.g.N * (double)insts[i].a.nviews, i});
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<int4> items;
+    for (const auto &oi : order) {
+        const int i = oi.second;
+        const BpTmaParams &a = insts[i].a;
+        const int tiles = plans[i]->od.nsq * a.tps * a.tps;
+        const int zs = (a.nz + kZT - 1) / kZT;
+        for (int t = 0; t < tiles; ++t)
+            for (int z = 0; z < zs; ++z) items.push_back(make_int4(i, t, z, 0));
+    }
+    supported = true;
+    cudaError_t e = ensure_smem<bp_persistent_kernel>(smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel, kThreads, smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    BatchImpl *b = new BatchImpl;
+    b->nitems = (int)items.size();
+    b->smem = smem;
+    b->grid = std::min(per_sm * sms, std::max(1, b->nitems));
+    if ((e = cudaMalloc(&b->maps, sizeof(CUtensorMap) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&b->insts, sizeof(BatchInst) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&b->items, sizeof(int4) * std::max<size_t>(1, items.size()))) != cudaSuccess ||
+        (e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(b->maps, maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->insts, insts.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+        batch_free_impl(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch(const BatchImpl &b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    bp_persistent_kernel<<<b.grid, kThreads, b.smem, st>>>(b.maps, b.insts, b.items, b.nitems, b.counter);
+    return cudaGetLastError();
+}
+
+void batch_destroy(BatchImpl *b) {
+    if (b) batch_free_impl(b);
 }
 
 }  // namespace fdkod

@@ -148,6 +148,16 @@ cudaError_t upload_net(PlanImpl &p);
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
                                float *vol, cudaStream_t st, Band b = Band{});
 
+// A batch of plans backprojected by one persistent launch (backproject.cu):
+// per plan its FDK-OD source (Q when D = 1, else the decomposed data) and
+// volume.  supported = false (and *out null) when a plan cannot take the
+// persistent path (its windows are not float32 or do not fit a TMA box).
+struct BatchImpl;
+cudaError_t batch_create(const PlanImpl *const *plans, const void *const *src, float *const *vols, int count,
+                         BatchImpl **out, bool &supported);
+cudaError_t batch_launch(const BatchImpl &b, cudaStream_t st);
+void batch_destroy(BatchImpl *b);
+
 }  // namespace fdkod
 
 struct fdkod_plan {

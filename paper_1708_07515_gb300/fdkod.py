@@ -78,6 +78,10 @@ def load():
                 "fdkod_get_decimation_net": (i, [vp, vp, i]),
                 "fdkod_net_adjoint": (i, [vp, vp, vp, i, vp, vp, u]),
                 "fdkod_net_backward": (i, [vp, vp, vp, vp, i, i, vp, u]),
+                "fdkod_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i,
+                                           ctypes.POINTER(vp)]),
+                "fdkod_batch_backproject": (i, [vp, u]),
+                "fdkod_batch_destroy": (None, [vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -224,6 +228,41 @@ def fdkod_net_backward(plan: int, Q, w, dS, row_lo: int, row_hi: int, dW, stream
                                      int(row_hi), _dev_ptr(dW, "dW"), _stream(dS, stream)), "fdkod_net_backward")
 
 
+class BatchBackprojection:
+    """fdkod_batch_create / fdkod_batch_backproject: the backprojections of
+    many plans in one persistent launch.  srcs[i]: Q (torch CUDA float32) for
+    a plan with D = 1, the decomposed data or None (the plan's workspace) for
+    D > 1; vols[i]: torch CUDA float32 [N][N][N].  Raises FdkodError
+    (status -2) when a plan cannot take the persistent path."""
+
+    def __init__(self, plans, srcs, vols):
+        n = len(plans)
+        arr = ctypes.c_void_p * n
+        P = arr(*[p.handle for p in plans])
+        S = arr(*[None if s is None else _dev_ptr(s, "src").value for s in srcs])
+        V = arr(*[_dev_ptr(v, "vol").value for v in vols])
+        out = ctypes.c_void_p()
+        _check(load().fdkod_batch_create(P, S, V, n, ctypes.byref(out)), "fdkod_batch_create")
+        self.handle = out.value
+        self._keep = (list(plans), list(srcs), list(vols))
+
+    def run(self, stream=None):
+        import torch
+        st = int(torch.cuda.current_stream().cuda_stream) if stream is None else int(stream)
+        _check(load().fdkod_batch_backproject(self.handle, st), "fdkod_batch_backproject")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().fdkod_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- convenience wrapper --------------------------------------------------
 
 class Plan:
@@ -297,6 +336,10 @@ class Plan:
         vol = self._vol(Q, vol)
         fdk_backproject_plain(self.handle, Q, vol, stream)
         return vol
+
+    def decompose_to_workspace(self, Q, stream=None):
+        """fdkod_decompose into the plan's own workspace (D > 1)."""
+        _check(load().fdkod_decompose(self.handle, _dev_ptr(Q, "Q"), None, _stream(Q, stream)), "fdkod_decompose")
 
     def decompose(self, Q, out=None, stream=None):
         import torch

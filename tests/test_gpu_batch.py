@@ -1,5 +1,6 @@
 """Batched reconstruction of volumes of uneven size in one CUDA graph, against
-eager launches (bit for bit) and against the FP64 oracle (parity bar)."""
+eager launches (bit for bit) and against the FP64 oracle (parity bar); the
+persistent batched backprojection against each plan's own launch."""
 import numpy as np
 import pytest
 
@@ -46,6 +47,39 @@ def test_graph_batch_matches_eager_and_oracle(fd, oracle_mod):
             rel = np.linalg.norm(got - want) / np.linalg.norm(want)
             assert rel <= 1e-5, (inst, rel)
         assert all(p.device_status() == 0 for p in br.plans)
+    finally:
+        br.close()
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_persistent_batch_equals_per_plan_launches(fd, oracle_mod, persistent):
+    """The persistent kernel (one launch, work list over volumes, tiles and
+    z-slabs; plans with D = 1 read Q, the others their workspace) gives each
+    volume bit for bit what its own backprojection launch gives."""
+    from paper_1708_07515_gb300.batch import BatchReconstructor, Instance
+    insts = [Instance(4.0 * 48, 48, 48, 48, 64, 2, 4), Instance(4.0 * 40, 40, 44, 36, 60, 0, 1),
+             Instance(4.0 * 64, 64, 64, 64, 90, 3, 3), Instance(4.0 * 33, 33, 36, 40, 48, 1, 2)]
+    projs = [phantom.project(phantom.make_phantom(4200 + k, i.N, 6), i.R, i.Nu, i.Nv, i.P)
+             for k, i in enumerate(insts)]
+    br = BatchReconstructor(insts, streams=3, persistent=persistent)
+    try:
+        assert (br.batch is not None) == persistent
+        br.load(projs)
+        br.capture()
+        br.replay()
+        torch.cuda.synchronize()
+        for inst, plan, Q, v in zip(insts, br.plans, br.Q, br.vol):
+            ref = plan.backproject(Q)
+            torch.cuda.synchronize()
+            assert torch.equal(v, ref), inst
+            assert plan.device_status() == 0
+        # and against the oracle (parity bar)
+        for inst, p, v in zip(insts, projs, br.vol):
+            Q = oracle_mod.filter(p, inst.R).astype(np.float32)
+            want = oracle_mod.fdkod(Q, inst.R, inst.N, inst.s, inst.D)
+            got = v.cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5, inst
+        assert br.launches() == sum(3 if i.D > 1 else 2 for i in insts) + (1 if persistent else len(insts))
     finally:
         br.close()
 
