@@ -271,7 +271,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
         // lanes 32 (w % 4) .. + 31 of tiles 4 (w / 4) .. + 3
         auto relu_to_operand = [&]() {
 #pragma unroll 1
-            for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
+            for (int i = wh * (kTiles / 2); i < (wh + 1) * (kTiles / 2); ++i) {
                 float z[16];
                 tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), z);
                 const int r = 128 * i + 32 * wq + lane;
@@ -294,15 +294,16 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
                 break;
             }
             // 1. layer-1 operand: a1 view ka (= view j0 D - 4 + ka) reads x at
-            // index ka + XL - 6 + t, t < 8; thread: column g, views 4 b .. 4 b + 3
+            // index ka + XL - 6 + t, t < 8; thread: column g, kVPT consecutive views
             {
-                const int g = tid & (kG - 1), b4 = (tid >> 4) * 4;
+                constexpr int kVPT = kNA1 * kG / kNetThreads;
+                const int g = tid & (kG - 1), b4 = (tid >> 4) * kVPT;
                 const float *xp = xs + (size_t)(b4 + ch.XL - 6) * kG + g;
-                float xw[11];
+                float xw[kVPT + 7];
 #pragma unroll
-                for (int t = 0; t < 11; ++t) xw[t] = xp[t * kG];
+                for (int t = 0; t < kVPT + 7; ++t) xw[t] = xp[t * kG];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < kVPT; ++i) {
                     const int r = (b4 + i) * kG + g;
                     *(uint4 *)(opa + (size_t)r * 16) =
                         make_uint4(bf16x2(xw[i], xw[i + 1]), bf16x2(xw[i + 2], xw[i + 3]),
@@ -368,7 +369,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             // whose MMAs are done): pm[ka2][m][g], m < 5
             float *pm = (float *)opa;
 #pragma unroll 1
-            for (int i = 4 * wh; i < 4 * wh + 4; ++i) {
+            for (int i = wh * (kTiles / 2); i < (wh + 1) * (kTiles / 2); ++i) {
                 float pz[16];
                 tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), pz);
                 const int ka2 = kTileViews * i + 2 * wq + (lane >> 4), g = lane & (kG - 1);
