@@ -99,3 +99,20 @@ def test_gpu_projector_matches_cpu_projector(fd):
     cpu = phantom.project(ell, R, N + 4, N - 6, P, dtype=np.float64)
     gpu = phantom.project_gpu(ell, R, N + 4, N - 6, P).cpu().numpy().astype(np.float64)
     assert np.abs(gpu - cpu).max() <= 2e-5 * np.abs(cpu).max()
+
+
+def test_batch_create_rejects_what_it_cannot_take(fd):
+    """A plan with 16-bit Q and D = 1 (16-bit windows) and a decimating plan
+    without a workspace are refused; the refusal leaves the plans usable."""
+    vol = torch.empty((32, 32, 32), device="cuda")
+    Q16 = torch.zeros((48, 32, 32), dtype=torch.bfloat16, device="cuda")
+    with fd.Plan(128.0, 32, 32, 32, 48, 1, 1, qtype="bf16") as p16, \
+            fd.Plan(128.0, 32, 32, 32, 48, 1, 4, workspace=False) as pnw:
+        with pytest.raises(fd.FdkodError) as e:
+            fd.BatchBackprojection([p16], [Q16], [vol])
+        assert e.value.status == -2
+        with pytest.raises(fd.FdkodError) as e:
+            fd.BatchBackprojection([pnw], [None], [vol])
+        assert e.value.status == -1
+        p16.backproject(Q16, vol)
+        assert p16.device_status() == 0

@@ -236,3 +236,41 @@ def test_net_backward_matches_oracle_vjp(fd, oracle_mod, D, rows):
     for lo, hi in [(0, 80), (80, 1360), (1360, 1440)]:
         rel = np.linalg.norm(got[lo:hi] - want[lo:hi]) / np.linalg.norm(want[lo:hi])
         assert rel <= 1e-4, (lo, hi, rel)
+
+
+def test_net_plans_that_cannot_take_it(fd):
+    """D = 1 (no decimation) and D above 60 reject a net; non-finite weights
+    and a wrong size are argument errors; a net-less plan reports none."""
+    with fd.Plan(128.0, 32, 32, 32, 48, 1, 1) as p1:
+        with pytest.raises(fd.FdkodError) as e:
+            p1.set_net(np.zeros(onet.NET_SIZE, np.float32))
+        assert e.value.status == -2
+        assert p1.net is None
+    with fd.Plan(128.0, 32, 32, 32, 128, 1, 64) as p64:
+        with pytest.raises(fd.FdkodError) as e:
+            p64.set_net(np.zeros(onet.NET_SIZE, np.float32))
+        assert e.value.status == -2
+    with fd.Plan(128.0, 32, 32, 32, 48, 1, 4) as p4:
+        bad = np.zeros(onet.NET_SIZE, np.float32)
+        bad[7] = np.nan
+        for w in (bad, np.zeros(10, np.float32)):
+            with pytest.raises(fd.FdkodError) as e:
+                p4.set_net(w)
+            assert e.value.status == -1
+        assert p4.net is None
+
+
+def test_net_with_taps_changed_after_setting_it(fd, oracle_mod):
+    """Setting new plain taps after the net keeps the net and uses the new
+    taps for the plain low-pass it adds to."""
+    N, P, s, D = 32, 48, 1, 4
+    R = 4.0 * N
+    Q = _scan(oracle_mod, 970, N, N, N, P, R)
+    w = _bf16_net(971)
+    h = oracle_mod.sinc_taps(D, 2)
+    with fd.Plan(R, N, N, N, P, s, D) as plan:
+        plan.set_net(w)
+        plan.set_taps(h)
+        got = plan.decompose(torch.from_numpy(Q).cuda()).cpu().numpy()
+        np.testing.assert_array_equal(plan.net, w.astype(np.float32))
+    _cmp_decomposed(got, oracle_mod, Q, R, N, s, D, w, taps=h, what="taps after net")
