@@ -48,7 +48,8 @@ constexpr int kTiles = 8;              // tiles per chunk
 constexpr int kNA1 = kTiles * kTileViews;  // a1 views per chunk (a2 rows are computed for as many)
 constexpr int kKA = kNA1 - 4;          // a2 views per chunk with their whole support
 constexpr int kRowsA = kNA1 * kG + 64; // operand rows: the layer-2 taps read 64 rows past the tiles
-constexpr int kPlaneA1 = kRowsA * 16;  // bytes of one 8-channel plane
+constexpr int kRowBytes = 32;          // operand row: 16 BF16 values, 32-byte swizzle layout
+constexpr int kOperandBytes = kRowsA * kRowBytes;
 constexpr int kNetThreads = 256;
 constexpr uint32_t kTmemCols = kTiles * 16;
 constexpr uint64_t kNetWaitNs = 2000000000ull;
@@ -107,7 +108,7 @@ __host__ __device__ inline NetChunk net_chunk(int D, int HD) {
 
 // dynamic shared memory of net_decompose_kernel (bytes, after 128-byte alignment)
 __host__ __device__ inline size_t net_smem(const NetChunk &c, int HD) {
-    return 2 * (size_t)kPlaneA1 + sizeof(uint16_t) * (kK + 2) * 256 + 2 * sizeof(float) * (size_t)c.NX * kG +
+    return (size_t)kOperandBytes + sizeof(uint16_t) * (kK + 2) * 256 + 2 * sizeof(float) * (size_t)c.NX * kG +
            sizeof(float) * (size_t)c.J * kG + sizeof(float) * (size_t)HD;
 }
 
@@ -154,7 +155,8 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
                      const NetWeights *__restrict__ net, int *status, int Tstride, int P, int D, int Pd, int HD,
                      int nrows, int Nu, int ngroups) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *base = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
+    // 1024-byte aligned (the swizzle pattern repeats every 256 bytes)
+    unsigned char *base = smem_raw + ((1024u - (tma::smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t bar, full[2], empty[2];
     __shared__ uint32_t tmem_slot;
 
@@ -174,7 +176,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
     }
     const NetChunk ch = net_chunk(D, HD);
     unsigned char *opa = base;                                      // operands: 2 planes of kRowsA rows
-    unsigned char *wb = opa + 2 * kPlaneA1;                         // W2 (5 x 512 B), W1 (512 B), W3 (512 B)
+    unsigned char *wb = opa + kOperandBytes;                        // W2 (5 x 512 B), W1 (512 B), W3 (512 B)
     float *xbuf = (float *)(wb + sizeof(uint16_t) * (kK + 2) * 256);  // 2 x [NX][kG]
     float *yacc = xbuf + 2 * (size_t)ch.NX * kG;                    // [J][kG]
     float *hs = yacc + (size_t)ch.J * kG;                           // [HD]
@@ -183,10 +185,8 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
         ((uint4 *)wb)[i] = ((const uint4 *)net->w2)[i];  // w2, b1, b3 are contiguous
     for (int i = tid; i < HD; i += kNetCtaThreads) hs[i] = net->h[i];
     // rows past the tiles: read by the tap offsets, must hold finite values
-    for (int i = tid; i < 2 * 64; i += kNetCtaThreads) {
-        const int pl = i / 64, r = kNA1 * kG + i % 64;
-        *(uint4 *)(opa + (size_t)pl * kPlaneA1 + (size_t)r * 16) = make_uint4(0u, 0u, 0u, 0u);
-    }
+    for (int i = tid; i < 2 * 64; i += kNetCtaThreads)
+        *(uint4 *)(opa + (size_t)(kNA1 * kG) * kRowBytes + (size_t)i * 16) = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         tma::mbar_init(&bar, 1);
         for (int b = 0; b < 2; ++b) {
@@ -239,11 +239,11 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
         const int wq = warp & 3, wh = warp >> 2;  // tensor-memory lane quarter, half of the tiles
         const uint32_t sopa = tma::smem_u32(opa), swb = tma::smem_u32(wb);
         constexpr uint32_t kIdesc = tc5::idesc_bf16_f32(128, 16);
-        // descriptors: operand planes (a1, a2: second plane kPlaneA1 on; the
-        // layer-1 operand has one plane, its second K half meets zero weights
-        // and is pointed 16 rows on), weights (two 256-byte planes)
-        const uint64_t dA12 = tc5::smem_desc(sopa, kPlaneA1, 128);
-        const uint64_t dX = tc5::smem_desc(sopa, 256, 128);
+        // descriptors: operands in the 32-byte swizzle layout (a row = 16
+        // values; a tile = 128 rows = 256 units of 16 bytes, a view = 16 rows
+        // = 32 units), weights unswizzled (two 256-byte planes)
+        const uint64_t dA12 = tc5::smem_desc_sw32(sopa, 256);
+        const uint64_t dX = dA12;
         const uint64_t dW2 = tc5::smem_desc(swb, 256, 128);
         const uint64_t dW1 = tc5::smem_desc(swb + kK * 512, 256, 128);
         const uint64_t dW3 = tc5::smem_desc(swb + (kK + 1) * 512, 256, 128);
@@ -275,9 +275,11 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
                 float z[16];
                 tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), z);
                 const int r = 128 * i + 32 * wq + lane;
-                *(uint4 *)(opa + (size_t)r * 16) = make_uint4(relu_bf16x2(z[0], z[1]), relu_bf16x2(z[2], z[3]),
-                                                              relu_bf16x2(z[4], z[5]), relu_bf16x2(z[6], z[7]));
-                *(uint4 *)(opa + kPlaneA1 + (size_t)r * 16) =
+                unsigned char *row = opa + (size_t)r * kRowBytes;
+                const int sw = (r >> 2) & 1;  // 16-byte halves swapped in rows 4-7 of each group of 8
+                *(uint4 *)(row + 16 * sw) = make_uint4(relu_bf16x2(z[0], z[1]), relu_bf16x2(z[2], z[3]),
+                                                       relu_bf16x2(z[4], z[5]), relu_bf16x2(z[6], z[7]));
+                *(uint4 *)(row + 16 * (sw ^ 1)) =
                     make_uint4(relu_bf16x2(z[8], z[9]), relu_bf16x2(z[10], z[11]), relu_bf16x2(z[12], z[13]),
                                relu_bf16x2(z[14], z[15]));
             }
@@ -305,9 +307,12 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
 #pragma unroll
                 for (int i = 0; i < kVPT; ++i) {
                     const int r = (b4 + i) * kG + g;
-                    *(uint4 *)(opa + (size_t)r * 16) =
+                    unsigned char *row = opa + (size_t)r * kRowBytes;
+                    const int sw = (r >> 2) & 1;
+                    *(uint4 *)(row + 16 * sw) =
                         make_uint4(bf16x2(xw[i], xw[i + 1]), bf16x2(xw[i + 2], xw[i + 3]),
                                    bf16x2(xw[i + 4], xw[i + 5]), bf16x2(xw[i + 6], xw[i + 7]));
+                    *(uint4 *)(row + 16 * (sw ^ 1)) = make_uint4(0u, 0u, 0u, 0u);  // taps 8-15: zero weights
                 }
             }
             operands_ready();
@@ -315,7 +320,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             if (tid == 0) {
 #pragma unroll 1
                 for (int i = 0; i < kTiles; ++i)
-                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dX + (uint64_t)(128 * i), dW1, kIdesc, 0u);
+                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dX + (uint64_t)(256 * i), dW1, kIdesc, 0u);
                 tc5::commit(&bar);
             }
             // plain low-pass meanwhile: output view j0 + jl, column g; then x
@@ -343,7 +348,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
                 for (int m = 0; m < kK; ++m)
 #pragma unroll 1
                     for (int i = 0; i < kTiles; ++i)
-                        tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i + 16 * m),
+                        tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(256 * i + 32 * m),
                                       dW2 + (uint64_t)(32 * m), kIdesc, m > 0 ? 1u : 0u);
                 tc5::commit(&bar);
             }
@@ -358,7 +363,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             if (tid == 0) {
 #pragma unroll 1
                 for (int i = 0; i < kTiles; ++i)
-                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(128 * i), dW3, kIdesc, 0u);
+                    tc5::mma_bf16(tmem + (uint32_t)(16 * i), dA12 + (uint64_t)(256 * i), dW3, kIdesc, 0u);
                 tc5::commit(&bar);
             }
             if (!mma_done()) {
@@ -408,7 +413,7 @@ template <typename TQ>
 cudaError_t launch_net_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows) {
     const int HD = p.tap_blocks * p.D;
     const NetChunk ch = net_chunk(p.D, HD);
-    const size_t smem = net_smem(ch, HD) + 128;
+    const size_t smem = net_smem(ch, HD) + 1024;
     cudaError_t e = ensure_smem<net_decompose_kernel<TQ>>(smem);
     if (e != cudaSuccess) return e;
     const int ngroups = (p.Tstride + kG - 1) / kG;

@@ -26,6 +26,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for a K-major operand in the 32-byte swizzle layout: rows of 32
+// bytes (16 16-bit values), 8-row groups of 256 bytes (stride-dimension
+// offset), the two 16-byte halves of a row swapped in rows 4-7 of each group;
+// swizzle mode 6 in bits 61-63 (the leading-dimension offset is unused).
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
