@@ -375,8 +375,8 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             float *pm = (float *)opa;
 #pragma unroll 1
             for (int i = wh * (kTiles / 2); i < (wh + 1) * (kTiles / 2); ++i) {
-                float pz[16];
-                tc5::ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), pz);
+                float pz[8];  // taps 0..4 (columns 5..15 are the zero-padded N)
+                tc5::ld8(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * i), pz);
                 const int ka2 = kTileViews * i + 2 * wq + (lane >> 4), g = lane & (kG - 1);
                 float *dst = pm + (size_t)ka2 * kK * kG + g;
 #pragma unroll
