@@ -95,14 +95,22 @@ def linear_fit(R: float, N: int, P: int, s: int, D: int, projs, zs, half: int = 
             G += gg
             b += bb
     tri = np.maximum(D - np.arange(m), 0) / float(D * D)
+    g = solve_correction(G, b, tri, n)
+    return {o: float(g[abs(o)]) for o in range(-half, half + 1)}
+
+
+def solve_correction(G: np.ndarray, b: np.ndarray, base: np.ndarray, n: int) -> np.ndarray:
+    """argmin over g (n taps g[|i|]) of 1/2 (base + g)^T G (base + g) - b^T g
+    subject to g_0 + 2 sum_{i>0} g_i = 0, with G, b over the first
+    len(base) taps (g zero past n): the KKT system of half + 2 unknowns."""
+    from . import learn
     c = learn.constraint(n)
     K = np.zeros((n + 1, n + 1))
     K[:n, :n] = G[:n, :n]
     K[:n, n] = c
     K[n, :n] = c
-    rhs = np.concatenate([b[:n] - G[:n] @ tri, [0.0]])
-    g = np.linalg.solve(K, rhs)[:n]
-    return {o: float(g[abs(o)]) for o in range(-half, half + 1)}
+    rhs = np.concatenate([b[:n] - G[:n] @ base, [0.0]])
+    return np.linalg.solve(K, rhs)[:n]
 
 
 class Adam:

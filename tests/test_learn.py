@@ -67,3 +67,34 @@ def test_net_linear_configuration_is_the_fir():
         x = rng.standard_normal((P, 5))
         want = sum(c * np.roll(x, -o, axis=0) for o, c in g.items())[::D]
         np.testing.assert_allclose(onet.net_forward(x, D, w), want, rtol=0, atol=1e-5 * np.abs(want).max())
+
+
+def test_net_trainer_host_logic():
+    """learn_net's host pieces: the row-interval union, Adam's first step
+    (sign of the gradient times the step size), and the zero-gain FIR
+    correction recovering a planted one from its normal equations."""
+    from paper_1708_07515_gb300 import learn_net
+    assert learn_net.merge_rows([(5, 9), (0, 3), (8, 12), (3, 4)]) == [(0, 4), (5, 12)]
+    assert learn_net.merge_rows([]) == []
+    opt = learn_net.Adam(4, lr=0.01)
+    w = opt.step(np.zeros(4, np.float32), np.array([1.0, -2.0, 0.5, 0.0]))
+    np.testing.assert_allclose(w, [-0.01, 0.01, -0.01, 0.0], atol=1e-6)
+    # a random SPD Gram matrix over 8 taps, a base filter, and a target made
+    # from base + g_true with c . g_true = 0: the solve recovers g_true
+    rng = np.random.default_rng(71)
+    A = rng.standard_normal((40, 8))
+    G = A.T @ A
+    base = np.array([0.25, 0.1875, 0.125, 0.0625, 0, 0, 0, 0])
+    n = 7
+    g_true = rng.standard_normal(n)
+    c = learn.constraint(n)
+    g_true -= c * (c @ g_true) / (c @ c)
+    total = base.copy()
+    total[:n] += g_true
+    b = G @ total                       # the normal equations' right side for that optimum
+    g = learn_net.solve_correction(G, b, base, n)
+    # the unconstrained optimum satisfies the constraint, so it is returned
+    np.testing.assert_allclose(g, g_true, atol=1e-9)
+    assert abs(c @ g) < 1e-12
+    w0 = learn_net.init_weights(3)
+    assert w0.shape == (1440,) and np.all(w0[1360:] == 0.0)
