@@ -213,3 +213,27 @@ def test_act_rounding_bound_covers_bf16_storage():
         b = net.act_rounding_bound(x, D, w)
         assert np.all(d <= b)
         assert d.max() > 0
+
+
+def test_act_rounding_bound_each_layer():
+    """Inputs built so that only one layer's input is off the BF16 grid: the
+    bound's term for that layer alone must cover the change (x exact and a1
+    exact: only a2 rounds; x off-grid with an identity-like layer 1: x and
+    a1 round)."""
+    rng = np.random.default_rng(53)
+    P, D = 40, 4
+    x = net.round_bf16(rng.standard_normal((P, 12)))          # on the BF16 grid
+    W1 = np.zeros((16, 5))
+    for c in range(16):
+        W1[c, c % 5] = 1.0 if c % 2 == 0 else -1.0             # a1 = relu(+-x[k + m - 2]): on the grid
+    W2 = rng.standard_normal((16, 16, 5)) * 0.3                 # z2 off the grid: only a2 rounds
+    W3 = rng.standard_normal((16, 5)) * 0.3
+    w = net.net_pack(W1, W2, W3)
+    d = np.abs(net.net_forward(x, D, w, act_round="bf16") - net.net_forward(x, D, w))
+    b = net.act_rounding_bound(x, D, w)
+    assert d.max() > 0
+    assert np.all(d <= b)
+    # x off the grid, same weights: x (and so a1) round as well
+    x2 = rng.standard_normal((P, 12))
+    d2 = np.abs(net.net_forward(x2, D, w, act_round="bf16") - net.net_forward(x2, D, w))
+    assert np.all(d2 <= net.act_rounding_bound(x2, D, w))
