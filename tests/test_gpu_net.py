@@ -79,6 +79,7 @@ def _cmp_decomposed(got, oracle_mod, Q, R, N, s, D, w, taps=None, what="", tight
     (24, 24, 20, 24, 1, 4, "triangle", "f32"),     # orbit shorter than one chunk
     (32, 32, 20, 120, 1, 60, "triangle", "f32"),   # largest D: one view per chunk
     (32, 32, 32, 48, 1, 4, "triangle", "bf16"),    # 16-bit Q
+    (40, 44, 36, 72, 2, 3, "triangle", "f16"),
 ])
 def test_net_decompose_matches_oracle(fd, oracle_mod, N, Nu, Nv, P, s, D, taps, qtype):
     R = 4.0 * N
