@@ -11,16 +11,18 @@
 //
 // Inference (net_decompose_kernel) keeps everything on chip: one CTA per
 // (square, detector row, 16 shifted columns) walks the orbit in chunks of
-// output views.  Per chunk it interpolates the shifted samples x from Q
-// (FP32), runs layer 1 on the CUDA cores (FP32, BF16 weights) and stores a1
-// as BF16 in the K-major operand layout of tc5.cuh, one MMA row per (view,
-// column).  Layer 2 is 8 tiles of 128 rows x 16 channels on the tensor cores:
-// per tile, five tcgen05.mma of K = 16 input channels, one per tap, whose A
-// operand is the a1 block started 16 m rows (m views) further down -- the
-// taps cost no data movement -- accumulating FP32 in tensor memory.  The
-// plain low-pass runs on the CUDA cores while the MMAs do; then each thread
-// reads its row of the accumulator (tcgen05.ld), applies the ReLU and adds
-// its layer-3 terms to the output views it feeds.
+// output views.  Two producer warps interpolate the shifted samples x of the
+// next chunk from Q (FP32) into a double-buffered tile; eight consumer warps
+// run the three layers as three rounds of tcgen05.mma on 8 tiles of 128
+// operand rows, one row per (view, column), BF16 operands in shared memory
+// (32-byte swizzle layout, tc5.cuh), FP32 accumulators in tensor memory:
+// layer 1 against W1 with the 8 view taps of x as K (an im2col row), layer
+// 2 as five MMAs per tile whose A operand starts 16 m rows (m views) further
+// down -- the taps cost no data movement -- and layer 3 with its 5 taps as
+// N.  Between rounds each thread reads its accumulator row (tcgen05.ld) and
+// writes ReLU + BF16 in one conversion; the plain low-pass of the output
+// views runs on the CUDA cores during the layer-1 round; the layer-3 terms
+// go through shared memory and each output view sums its five.
 //
 // Training (CUDA cores, FP32): net_adjoint_kernel applies the adjoint of the
 // backprojection to a residual volume (the gradient of the reconstruction
