@@ -138,15 +138,15 @@ __device__ __forceinline__ bool consumers_and(bool v) {
 // tensor cores, M = 128 rows x N = 16 per tile, 8 tiles, FP32 in tensor
 // memory, BF16 operands in shared memory):
 //   1. layer-1 operand: row (view, column) = x at views view - 2 .. view + 5
-//      (BF16; taps 5..7 meet zero weights)
+//      (BF16; taps 5..7, and the row's second 16 bytes, meet zero weights)
 //   2. z1 = one MMA per tile against W1 (K = 16 taps); meanwhile the plain
 //      low-pass of the chunk's output views (FP32, from x)
-//   3. a1 = relu(z1) as BF16, two 8-channel planes
+//   3. a1 = relu(z1) as BF16, one 32-byte row of 16 channels per operand row
 //   4. z2 = five MMAs per tile, tap m reading a1 from row 16 m on (K = 16 channels)
 //   5. a2 = relu(z2) as BF16, over a1
 //   6. p = one MMA per tile against W3 (N = its 5 taps, zero-padded)
-//   7. each row adds p[m] to the output view it feeds through tap m
-//   8. store
+//   7. each row's p[0..4] to shared memory
+//   8. output view = plain low-pass + the five p[m] of the rows it reads; store
 constexpr int kProducerWarps = 2;
 constexpr int kNetCtaThreads = kNetThreads + 32 * kProducerWarps;
 
@@ -177,7 +177,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
         return;
     }
     const NetChunk ch = net_chunk(D, HD);
-    unsigned char *opa = base;                                      // operands: 2 planes of kRowsA rows
+    unsigned char *opa = base;                                      // operands: kRowsA rows of 32 bytes
     unsigned char *wb = opa + kOperandBytes;                        // W2 (5 x 512 B), W1 (512 B), W3 (512 B)
     float *xbuf = (float *)(wb + sizeof(uint16_t) * (kK + 2) * 256);  // 2 x [NX][kG]
     float *yacc = xbuf + 2 * (size_t)ch.NX * kG;                    // [J][kG]
@@ -269,7 +269,7 @@ net_decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ out, const in
             consumers_sync();
             tc5::fence_after_sync();
         };
-        // relu of tensor-memory rows -> BF16 operand planes; warp w reads
+        // relu of tensor-memory rows -> BF16 operand rows; warp w reads
         // lanes 32 (w % 4) .. + 31 of tiles 4 (w / 4) .. + 3
         auto relu_to_operand = [&]() {
 #pragma unroll 1
