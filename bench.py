@@ -303,7 +303,7 @@ def batched_main(args):
     insts = [Instance(R, N, N, N, P) for N, P, R, _ in work]
     projs = [phantom.project_gpu(phantom.make_phantom(sd, N, 20), R, N, N, P) for N, P, R, sd in work]
     rates = autotune.measure_rates()
-    br = BatchReconstructor(insts, rates=rates, persistent=args.persistent)
+    br = BatchReconstructor(insts, rates=rates, persistent=args.persistent, tune_tiles=True)
     br.load(projs)
     br.capture()
     for _ in range(args.warmup):
@@ -325,6 +325,7 @@ def batched_main(args):
            "config": {"workload": "batched_64_volumes_N64-384_P1.4N", "volumes": len(insts),
                       "step": "one CUDA-graph launch: bounds + filter + decompose + backproject of every volume",
                       "streams": len(br.lanes), "persistent_backprojection": br.batch is not None,
+                      "tile_widths": br.tiles,
                       "choices": [[i.N, i.P, i.s, i.D] for i in insts], "rates": list(rates)},
            "gpu_launches": br.launches() * args.steps, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)

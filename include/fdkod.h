@@ -167,7 +167,8 @@ int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t str
  * fdkod_backproject for D > 1, reading decomposed data S (device, the
  * layout fdkod_decompose writes) instead of the plan's workspace.  With
  * fdkod_decompose it splits fdkod_backproject into its two kernels, e.g.
- * to time them apart.  Errors: INVALID_ARG (also when D == 1), CUDA.
+ * to time them apart.  S NULL reads the plan's own workspace.  Errors:
+ * INVALID_ARG (also when D == 1, or S NULL without a workspace), CUDA.
  */
 int fdkod_backproject_decomposed(fdkod_plan_t *plan, const float *S, float *vol, uintptr_t stream);
 
@@ -392,6 +393,22 @@ int fdkod_batch_create(fdkod_plan_t *const *plans, const void *const *src, float
                        fdkod_batch_t **out);
 int fdkod_batch_backproject(fdkod_batch_t *batch, uintptr_t stream);
 void fdkod_batch_destroy(fdkod_batch_t *batch);
+
+/*
+ * Tile shape of the FDK-OD backprojection (for an autotuner): each CTA
+ * stages, per view, a window of the source covering its 16 x 16 x 32-voxel
+ * tile's footprint; the window width (columns) is one of the instantiated
+ * 32, 48, 64, 96, 128.  By default a plan takes the narrowest one that holds
+ * every tile's footprint.  fdkod_set_tile(plan, cols) selects a wider one
+ * (cols = 0: back to the default); results are the same bit for bit, only
+ * the shared-memory layout (bank conflicts) and occupancy change.
+ * fdkod_get_tile returns the width in use (float32 windows) and the
+ * narrowest valid one (0 when no window fits: the unstaged kernels run).
+ * Call while no launch of the plan is in flight.  Errors: INVALID_ARG,
+ * UNSUPPORTED (a width that is not instantiated or too narrow).
+ */
+int fdkod_set_tile(fdkod_plan_t *plan, int window_cols);
+int fdkod_get_tile(const fdkod_plan_t *plan, int *window_cols, int *min_cols);
 
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);

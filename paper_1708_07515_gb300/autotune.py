@@ -8,6 +8,9 @@ rate, each measured on one small probe plan, give
     t_rec(s, D) = N^3 (P / D) / rate_bp
     t_dec(s)    = sum_q P Nv T_q / rate_dec ~ kappa 2^s N Nv P / rate_dec,
 and a short measured search around the model's optimum picks the plan.
+choose_tile then picks the backprojection's tile shape -- the width of the
+staging window each 16 x 16 x 32-voxel tile reads per view (fdkod_set_tile)
+-- by timing the plan's own backprojection with each valid width.
 D is kept a divisor of P and at most 2^s (one decimation stage per
 decomposition stage, Sec. 2.2); `skip` lowers it by that many stages for
 quality (the paper skips one stage in its measurements, Sec. 3).
@@ -98,3 +101,44 @@ def choose(N: int, P: int, rate_bp: float, rate_dec: float, skip: int = 0, smax:
             c.measured_ms = float(timer(c.s, c.D))
             tried.append(c)
     return min(tried, key=lambda c: c.measured_ms)
+
+
+TILE_WIDTHS = (32, 48, 64, 96, 128)
+
+
+def tile_candidates(min_cols: int, count: int = 3) -> list[int]:
+    """The narrowest valid staging-window width and the next wider ones."""
+    return [w for w in TILE_WIDTHS if w >= min_cols][:count] if min_cols > 0 else []
+
+
+def choose_tile(plan, reps: int = 3, count: int = 3) -> tuple[int, dict]:
+    """Time the plan's FDK-OD backprojection (from its decomposed workspace,
+    or from Q when D = 1) with each candidate window width, keep the fastest
+    (set on the plan) and return (width, {width: ms}).  Data values do not
+    change the timing, so zero inputs serve."""
+    import torch
+    _, narrowest = plan.tile
+    cands = tile_candidates(narrowest, count)
+    if len(cands) < 2:
+        return plan.tile[0], {}
+    Q = torch.zeros((plan.P, plan.Nv, plan.Nu), dtype=plan.q_torch_dtype, device="cuda")
+    vol = torch.empty((plan.N, plan.N, plan.N), dtype=torch.float32, device="cuda")
+    if plan.D > 1:
+        plan.decompose_to_workspace(Q)
+    times = {}
+    for w in cands:
+        plan.set_tile(w)
+        run = (lambda: plan.backproject(Q, vol)) if plan.D == 1 else \
+            (lambda: plan.backproject_decomposed_workspace(vol))
+        run()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            run()
+        b.record()
+        torch.cuda.synchronize()
+        times[w] = a.elapsed_time(b) / reps
+    best = min(times, key=times.get)
+    plan.set_tile(best)
+    return best, times

@@ -55,7 +55,7 @@ class Instance:
 
 class BatchReconstructor:
     def __init__(self, instances: list[Instance], qtype: str = "f32", rates: tuple[float, float] | None = None,
-                 skip: int = 0, streams: int = 4, persistent: bool = False):
+                 skip: int = 0, streams: int = 4, persistent: bool = False, tune_tiles: bool = False):
         import torch
         self.torch = torch
         self.instances = instances
@@ -72,6 +72,9 @@ class BatchReconstructor:
             self.proj.append(torch.empty((inst.P, inst.Nv, inst.Nu), dtype=torch.float32, device="cuda"))
             self.Q.append(torch.empty((inst.P, inst.Nv, inst.Nu), dtype=plan.q_torch_dtype, device="cuda"))
             self.vol.append(torch.empty((inst.N, inst.N, inst.N), dtype=torch.float32, device="cuda"))
+        # tile shape per volume (the backprojection's staging-window width),
+        # timed on the volume's own plan
+        self.tiles = [autotune.choose_tile(p)[0] if tune_tiles else p.tile[0] for p in self.plans]
         self.graph = None
         self.stream = torch.cuda.Stream()
         self.lanes = [torch.cuda.Stream() for _ in range(max(1, streams))]

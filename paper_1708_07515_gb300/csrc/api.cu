@@ -119,6 +119,8 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     // TMA copies start on a 16-byte boundary: up to 3 more float32 columns,
     // or 7 more 16-bit columns
     const int need = (int)ceil(ext_t) + 8, need16 = (int)ceil(ext_t) + 12;
+    ss.need = need;
+    ss.need16 = need16;
     ss.WdT = ss.WdT16 = 0;
     for (int w : {128, 96, 64, 48, 32}) {
         if (need <= w) ss.WdT = w;
@@ -395,7 +397,9 @@ int fdkod_decompose(fdkod_plan_t *plan, const void *Q, float *out, uintptr_t str
 }
 
 int fdkod_backproject_decomposed(fdkod_plan_t *plan, const float *S, float *vol, uintptr_t stream) {
-    if (!plan || !S || !vol || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    if (!plan || !vol || plan->impl.D == 1) return FDKOD_ERR_INVALID_ARG;
+    if (!S) S = plan->impl.Sp;  // the plan's own workspace
+    if (!S) return FDKOD_ERR_INVALID_ARG;
     return cuda_status(launch_backproject(plan->impl, plan->impl.od, false, S, vol, (cudaStream_t)stream));
 }
 
@@ -569,4 +573,37 @@ void fdkod_batch_destroy(fdkod_batch_t *batch) {
     if (!batch) return;
     fdkod::batch_destroy(batch->impl);
     delete batch;
+}
+
+namespace {
+constexpr int kTileWidths[] = {32, 48, 64, 96, 128};  // the backprojection's instantiated windows
+int auto_width(int need) {
+    for (int w : kTileWidths)
+        if (need <= w) return w;
+    return 0;
+}
+}  // namespace
+
+int fdkod_set_tile(fdkod_plan_t *plan, int window_cols) {
+    if (!plan || window_cols < 0) return FDKOD_ERR_INVALID_ARG;
+    fdkod::SquareSet &ss = plan->impl.od;
+    if (window_cols == 0) {
+        ss.WdT = auto_width(ss.need);
+        ss.WdT16 = auto_width(ss.need16);
+        return FDKOD_OK;
+    }
+    bool instantiated = false;
+    for (int w : kTileWidths) instantiated = instantiated || w == window_cols;
+    if (!instantiated || window_cols < ss.need || ss.Rw > 256) return FDKOD_ERR_UNSUPPORTED;
+    ss.WdT = window_cols;
+    ss.WdT16 = window_cols >= ss.need16 ? window_cols : auto_width(ss.need16);
+    return FDKOD_OK;
+}
+
+int fdkod_get_tile(const fdkod_plan_t *plan, int *window_cols, int *min_cols) {
+    if (!plan) return FDKOD_ERR_INVALID_ARG;
+    const fdkod::SquareSet &ss = plan->impl.od;
+    if (window_cols) *window_cols = ss.WdT;
+    if (min_cols) *min_cols = auto_width(ss.need);
+    return FDKOD_OK;
 }

@@ -39,6 +39,7 @@ struct SquareSet {
     // (4-element alignment slack, rounded up to a kernel instantiation, 0
     // when no instantiation is wide enough)
     int Wd = 0, Rw = 0, WdT = 0, WdT16 = 0;  // WdT16: the same for 16-bit windows
+    int need = 0, need16 = 0;  // the narrowest TMA windows that hold every tile's footprint
     int tiles_per_side = 1;  // 16-voxel tiles per square side
 };
 

@@ -82,6 +82,8 @@ def load():
                                            ctypes.POINTER(vp)]),
                 "fdkod_batch_backproject": (i, [vp, u]),
                 "fdkod_batch_destroy": (None, [vp]),
+                "fdkod_set_tile": (i, [vp, i]),
+                "fdkod_get_tile": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -349,6 +351,13 @@ class Plan:
         fdkod_decompose(self.handle, Q, out, stream)
         return out
 
+    def backproject_decomposed_workspace(self, vol, stream=None):
+        """The FDK-OD backprojection of the plan's own decomposed workspace
+        (what fdkod_backproject runs after its decomposition)."""
+        _check(load().fdkod_backproject_decomposed(self.handle, None, _dev_ptr(vol, "vol"), _stream(vol, stream)),
+               "fdkod_backproject_decomposed")
+        return vol
+
     def backproject_decomposed(self, S, vol=None, stream=None):
         vol = self._vol(S, vol)
         fdkod_backproject_decomposed(self.handle, S, vol, stream)
@@ -394,6 +403,17 @@ class Plan:
     def set_taps(self, taps) -> None:
         """Replace the angular low-pass taps (D or 2D values h[|i|])."""
         fdkod_set_decimation_taps(self.handle, taps)
+
+    @property
+    def tile(self) -> tuple[int, int]:
+        """(window columns in use, narrowest valid) of the FDK-OD backprojection."""
+        w, m = ctypes.c_int(), ctypes.c_int()
+        _check(load().fdkod_get_tile(self.handle, ctypes.byref(w), ctypes.byref(m)), "fdkod_get_tile")
+        return w.value, m.value
+
+    def set_tile(self, window_cols: int) -> None:
+        """Select the backprojection's staging-window width (0: default)."""
+        _check(load().fdkod_set_tile(self.handle, int(window_cols)), "fdkod_set_tile")
 
     @property
     def net(self):

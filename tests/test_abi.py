@@ -61,6 +61,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.fdkod_net_adjoint(None, None, None, 0, None, None, 0) == -1
     assert lib.fdkod_net_backward(None, None, None, None, 0, 1, None, 0) == -1
     assert lib.fdkod_batch_create(None, None, None, 0, None) == -1
+    assert lib.fdkod_set_tile(None, 0) == -1
+    assert lib.fdkod_get_tile(None, None, None) == -1
     assert lib.fdkod_batch_backproject(None, 0) == -1
     lib.fdkod_batch_destroy(None)
     for rc in (0, -1, -2, -3, -4, -5, -6, 99):

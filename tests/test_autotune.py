@@ -58,3 +58,11 @@ def test_lane_assignment_balances_longest_first():
     # one lane: everything on it; more lanes than volumes: one volume each
     assert assign_lanes(costs, 1) == [0] * 6
     assert sorted(assign_lanes(costs[:3], 5)) == [0, 1, 2]
+
+
+def test_tile_candidates():
+    from paper_1708_07515_gb300 import autotune
+    assert autotune.tile_candidates(48) == [48, 64, 96]
+    assert autotune.tile_candidates(96, count=5) == [96, 128]
+    assert autotune.tile_candidates(128) == [128]
+    assert autotune.tile_candidates(0) == []

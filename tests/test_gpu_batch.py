@@ -116,3 +116,32 @@ def test_batch_create_rejects_what_it_cannot_take(fd):
         assert e.value.status == -1
         p16.backproject(Q16, vol)
         assert p16.device_status() == 0
+
+
+def test_tile_width_choice_keeps_results(fd):
+    """Every valid staging-window width gives the same volume bit for bit;
+    too narrow or uninstantiated widths are refused; the autotuner's choice
+    is one of the candidates and stays set on the plan."""
+    from paper_1708_07515_gb300 import autotune
+    N, P = 64, 90
+    R = 4.0 * N
+    Q = torch.from_numpy(np.random.default_rng(4300).standard_normal((P, N, N)).astype(np.float32)).cuda()
+    for s, D in ((2, 3), (1, 1)):
+        with fd.Plan(R, N, N, N, P, s, D) as plan:
+            cur, narrowest = plan.tile
+            assert cur == narrowest > 0
+            ref = plan.backproject(Q).clone()
+            for w in autotune.tile_candidates(narrowest, count=5):
+                plan.set_tile(w)
+                assert plan.tile[0] == w
+                assert torch.equal(plan.backproject(Q), ref), (s, D, w)
+            for bad in (narrowest - 16, 40):
+                if bad > 0 and bad not in autotune.TILE_WIDTHS or bad < narrowest:
+                    with pytest.raises(fd.FdkodError):
+                        plan.set_tile(bad)
+            plan.set_tile(0)
+            assert plan.tile[0] == narrowest
+            best, times = autotune.choose_tile(plan)
+            assert best in times and plan.tile[0] == best
+            assert torch.equal(plan.backproject(Q), ref)
+            assert plan.device_status() == 0
