@@ -91,3 +91,31 @@ def test_library_sinc_taps_match_the_oracle(lib, oracle_mod, D, H):
     got = F.fdkod_sinc_taps(D, H)
     np.testing.assert_allclose(got, oracle_mod.sinc_taps(D, H), rtol=0, atol=1e-15)
     assert lib.fdkod_sinc_taps(D, 3, None) == -1
+
+
+def test_binding_signatures_match_the_header():
+    """The binding declares every prototype of include/fdkod.h, and nothing
+    else, with the same number of parameters."""
+    import re as _re
+    src = open(os.path.join(ROOT, "include", "fdkod.h")).read()
+    src = _re.sub(r"/\*.*?\*/", "", src, flags=_re.S)
+    protos = {}
+    for m in _re.finditer(r"\b((?:fdkod|fdk)_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src, flags=_re.S):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    binding = open(os.path.join(ROOT, "paper_1708_07515_gb300", "fdkod.py")).read()
+    table = binding[binding.index("sig = {"):binding.index("for name, (res, args) in sig.items()")]
+    bound = {}
+    for m in _re.finditer(r'"((?:fdkod|fdk)_[a-z_]+)":\s*\(([^\[]*)\[(.*?)\]\)', table, flags=_re.S):
+        inner = m.group(3)
+        depth, n = 0, 0
+        for ch in inner:
+            depth += ch in "(["
+            depth -= ch in ")]"
+            if ch == "," and depth == 0:
+                n += 1
+        bound[m.group(1)] = 0 if not inner.strip() else n + 1
+    assert len(protos) >= 30
+    assert set(bound) == set(protos), set(bound) ^ set(protos)
+    for name, n in bound.items():
+        assert protos[name] == n, (name, protos[name], n)
