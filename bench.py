@@ -216,7 +216,7 @@ def recorded_bp_traffic(workload: str):
         text = open(os.path.join(ROOT, "profiles", "dram_traffic_fdkod_512.md")).read()
         src = open(os.path.join(ROOT, "paper_1708_07515_gb300", "csrc", "backproject.cu")).read()
         a = src.index("template <typename TS, bool DIRECT, int WD>\n__global__")
-        b = src.index("template <typename TS, bool DIRECT, int WD>\ncudaError_t launch_tma_t")
+        b = src.index("\n}\n", a) + 3  # the kernel's closing brace
         fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith("bp_traffic_"))
         if fields.get("bp_traffic_workload") != workload:
             return None
