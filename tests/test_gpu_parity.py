@@ -13,6 +13,9 @@ Inputs: seeded random-ellipsoid phantoms (phantom module), their exact
 projections, filtered by the oracle in FP64 and rounded to float32 so both
 sides read identical Q values.
 """
+import glob
+import os
+
 import numpy as np
 import pytest
 
@@ -74,6 +77,24 @@ def test_bounds_bit_exact(fd, oracle_mod, R, N, Nu, P, s):
     for key in ("lo", "hi", "crop", "w0", "T"):
         assert np.array_equal(got[key], want[key]), key
     assert np.array_equal(got["phi"].view(np.int64), want["phi"].view(np.int64))
+    plan.close()
+
+
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bounds_*.txt")))
+
+
+@pytest.mark.parametrize("path", GOLDEN, ids=os.path.basename)
+def test_bounds_equal_the_stored_fixtures(fd, path):
+    """The library's bounds against the stored oracle values of
+    tests/golden (no oracle call at run time)."""
+    from test_golden import _read
+    g = _read(path)
+    R, N, Nu, P, s = g["geometry"]
+    plan = fd.Plan(R, N, Nu, N, P, s, 1)
+    got = plan.bounds()
+    for key in ("lo", "hi", "crop", "w0", "T"):
+        assert np.array_equal(got[key], g[key]), key
+    assert np.array_equal(got["phi"].view(np.int64), g["phi"].view(np.int64))
     plan.close()
 
 
