@@ -333,8 +333,8 @@ int fdkod_sinc_taps(int D, int H, double *h);
  *   S'[j]   += sum_{c,m} W3[c][m] a2[c][jD+m-2]
  * Weights: FDKOD_NET_SIZE floats, W1 [16][5], then W2 [16][16][5] (output
  * channel, input channel, tap), then W3 [16][5].  Inference stores them as
- * BF16 (round to nearest even), keeps a1 as BF16 and accumulates in FP32;
- * layer 2 runs on the tensor cores.
+ * BF16 (round to nearest even), rounds each layer's input (x, a1, a2) to
+ * BF16 and accumulates in FP32; all three layers run on the tensor cores.
  *
  * fdkod_set_decimation_net: copy w (host, not retained) into the plan; w
  *   NULL removes the net (plain low-pass again).  Synchronous; call it

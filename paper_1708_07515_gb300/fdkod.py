@@ -114,6 +114,23 @@ def _dev_ptr(t, what):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _expect(t, shape, dtype, what, at_least=False):
+    """The checks the C interface cannot make (it takes bare pointers): t is
+    a contiguous CUDA tensor of `dtype` whose shape is `shape` (None entries
+    match any extent), or, with at_least, a flat buffer of at least
+    `shape` elements.  Raises ValueError."""
+    if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype}, not {t.dtype}")
+    if at_least:
+        if t.numel() < int(shape):
+            raise ValueError(f"{what} holds {t.numel()} elements, needs {int(shape)}")
+    elif len(t.shape) != len(shape) or any(e is not None and int(g) != int(e) for g, e in zip(t.shape, shape)):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    return t
+
+
 # ---- C-named functions -------------------------------------------------------
 
 FDKOD_PLAN_NO_WORKSPACE = 1
@@ -238,7 +255,17 @@ class BatchBackprojection:
     (status -2) when a plan cannot take the persistent path."""
 
     def __init__(self, plans, srcs, vols):
+        import torch
         n = len(plans)
+        if len(srcs) != n or len(vols) != n:
+            raise ValueError("one source and one volume per plan")
+        for p, src, vol in zip(plans, srcs, vols):
+            _expect(vol, p.vol_shape, torch.float32, "vol")
+            if src is not None:
+                if p.D == 1:
+                    _expect(src, p.q_shape, p.q_torch_dtype, "src (Q)")
+                else:
+                    _expect(src, p.decomposed_shape, torch.float32, "src (decomposed data)")
         arr = ctypes.c_void_p * n
         P = arr(*[p.handle for p in plans])
         S = arr(*[None if s is None else _dev_ptr(s, "src").value for s in srcs])
@@ -316,49 +343,71 @@ class Plan:
         import torch
         return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[self.qtype]
 
+    # shapes of the device arrays the entry points read and write
+    @property
+    def q_shape(self):
+        return (self.P, self.Nv, self.Nu)
+
+    @property
+    def vol_shape(self):
+        return (self.N, self.N, self.N)
+
+    @property
+    def decomposed_shape(self):
+        return (self.info["n_squares"], self.info["Pd"], self.Nv, self.info["T_stride"])
+
+    def _q(self, Q, what="Q"):
+        return _expect(Q, self.q_shape, self.q_torch_dtype, what)
+
     def filter(self, proj, Q=None, stream=None):
         import torch
+        _expect(proj, self.q_shape, torch.float32, "proj")
         if Q is None:
-            Q = torch.empty((self.P, self.Nv, self.Nu), dtype=self.q_torch_dtype, device=proj.device)
-        fdkod_filter(self.handle, proj, Q, stream)
+            Q = torch.empty(self.q_shape, dtype=self.q_torch_dtype, device=proj.device)
+        fdkod_filter(self.handle, proj, self._q(Q), stream)
         return Q
 
     def _vol(self, Q, vol):
         import torch
         if vol is None:
-            vol = torch.empty((self.N, self.N, self.N), dtype=torch.float32, device=Q.device)
-        return vol
+            vol = torch.empty(self.vol_shape, dtype=torch.float32, device=Q.device)
+        return _expect(vol, self.vol_shape, torch.float32, "vol")
 
     def backproject(self, Q, vol=None, stream=None):
-        vol = self._vol(Q, vol)
+        vol = self._vol(self._q(Q), vol)
         fdkod_backproject(self.handle, Q, vol, stream)
         return vol
 
     def backproject_plain(self, Q, vol=None, stream=None):
-        vol = self._vol(Q, vol)
+        vol = self._vol(self._q(Q), vol)
         fdk_backproject_plain(self.handle, Q, vol, stream)
         return vol
 
     def decompose_to_workspace(self, Q, stream=None):
         """fdkod_decompose into the plan's own workspace (D > 1)."""
-        _check(load().fdkod_decompose(self.handle, _dev_ptr(Q, "Q"), None, _stream(Q, stream)), "fdkod_decompose")
+        _check(load().fdkod_decompose(self.handle, _dev_ptr(self._q(Q), "Q"), None, _stream(Q, stream)),
+               "fdkod_decompose")
 
     def decompose(self, Q, out=None, stream=None):
         import torch
-        shape = (self.info["n_squares"], self.info["Pd"], self.Nv, self.info["T_stride"])
+        self._q(Q)
         if out is None:
-            out = torch.empty(shape, dtype=torch.float32, device=Q.device)
-        fdkod_decompose(self.handle, Q, out, stream)
+            out = torch.empty(self.decomposed_shape, dtype=torch.float32, device=Q.device)
+        fdkod_decompose(self.handle, Q, _expect(out, self.decomposed_shape, torch.float32, "out"), stream)
         return out
 
     def backproject_decomposed_workspace(self, vol, stream=None):
         """The FDK-OD backprojection of the plan's own decomposed workspace
         (what fdkod_backproject runs after its decomposition)."""
+        import torch
+        _expect(vol, self.vol_shape, torch.float32, "vol")
         _check(load().fdkod_backproject_decomposed(self.handle, None, _dev_ptr(vol, "vol"), _stream(vol, stream)),
                "fdkod_backproject_decomposed")
         return vol
 
     def backproject_decomposed(self, S, vol=None, stream=None):
+        import torch
+        _expect(S, self.decomposed_shape, torch.float32, "S")
         vol = self._vol(S, vol)
         fdkod_backproject_decomposed(self.handle, S, vol, stream)
         return vol
@@ -376,8 +425,10 @@ class Plan:
 
     def filter_rows(self, proj_rows, v0: int, Q=None, stream=None):
         import torch
+        _expect(proj_rows, (self.P, None, self.Nu), torch.float32, "proj_rows")
         if Q is None:
             Q = torch.empty(proj_rows.shape, dtype=self.q_torch_dtype, device=proj_rows.device)
+        _expect(Q, tuple(proj_rows.shape), self.q_torch_dtype, "Q_rows")
         _check(load().fdkod_filter_rows(self.handle, _dev_ptr(proj_rows, "proj_rows"), int(v0), int(proj_rows.shape[1]),
                                         _dev_ptr(Q, "Q_rows"), _stream(proj_rows, stream)), "fdkod_filter_rows")
         return Q
@@ -387,8 +438,12 @@ class Plan:
 
     def backproject_slab(self, Q_rows, v0: int, S_work, z0: int, nz: int, vol=None, stream=None):
         import torch
+        _expect(Q_rows, (self.P, None, self.Nu), self.q_torch_dtype, "Q_rows")
+        if S_work is not None:
+            _expect(S_work, self.slab_workspace_elems(Q_rows.shape[1]), torch.float32, "S_work", at_least=True)
         if vol is None:
             vol = torch.empty((nz, self.N, self.N), dtype=torch.float32, device=Q_rows.device)
+        _expect(vol, (nz, self.N, self.N), torch.float32, "vol_slab")
         sw = _dev_ptr(S_work, "S_work") if S_work is not None else ctypes.c_void_p()
         _check(load().fdkod_backproject_slab(self.handle, _dev_ptr(Q_rows, "Q_rows"), int(v0), int(Q_rows.shape[1]), sw,
                                              int(z0), int(nz), _dev_ptr(vol, "vol_slab"), _stream(Q_rows, stream)),
@@ -425,9 +480,19 @@ class Plan:
         fdkod_set_decimation_net(self.handle, w)
 
     def net_adjoint(self, vol_slice, ref_slice, z: int, dS, sq_err, stream=None) -> None:
+        import torch
+        _expect(vol_slice, (self.N, self.N), torch.float32, "vol_slice")
+        _expect(ref_slice, (self.N, self.N), torch.float32, "ref_slice")
+        _expect(dS, self.decomposed_shape, torch.float32, "dS")
+        _expect(sq_err, 1, torch.float32, "sq_err", at_least=True)
         fdkod_net_adjoint(self.handle, vol_slice, ref_slice, z, dS, sq_err, stream)
 
     def net_backward(self, Q, w, dS, row_lo: int, row_hi: int, dW, stream=None) -> None:
+        import torch
+        self._q(Q)
+        _expect(w, (FDKOD_NET_SIZE,), torch.float32, "w")
+        _expect(dS, self.decomposed_shape, torch.float32, "dS")
+        _expect(dW, (FDKOD_NET_SIZE,), torch.float32, "dW")
         fdkod_net_backward(self.handle, Q, w, dS, row_lo, row_hi, dW, stream)
 
     def bounds(self) -> dict:

@@ -119,3 +119,40 @@ def test_binding_signatures_match_the_header():
     assert set(bound) == set(protos), set(bound) ^ set(protos)
     for name, n in bound.items():
         assert protos[name] == n, (name, protos[name], n)
+
+
+class _FakeDev:
+    """Stands in for a CUDA tensor (attributes only; nothing is launched)."""
+
+    def __init__(self, shape, dtype, contiguous=True):
+        self.is_cuda, self.shape, self.dtype, self._c = True, tuple(shape), dtype, contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        n = 1
+        for e in self.shape:
+            n *= int(e)
+        return n
+
+
+def test_binding_checks_what_the_bare_pointers_cannot():
+    """The Plan methods check shape, dtype and layout before a pointer
+    reaches the library, so a wrongly sized tensor is a ValueError, not an
+    out-of-bounds access on the device."""
+    torch = pytest.importorskip("torch")
+    from paper_1708_07515_gb300 import fdkod as F
+    ok = _FakeDev((4, 5, 6), torch.float32)
+    assert F._expect(ok, (4, 5, 6), torch.float32, "x") is ok
+    assert F._expect(ok, (4, None, 6), torch.float32, "x") is ok
+    assert F._expect(ok, 120, torch.float32, "x", at_least=True) is ok
+    for bad, shape, dtype in [(_FakeDev((4, 5, 6), torch.float64), (4, 5, 6), torch.float32),
+                              (_FakeDev((4, 5, 7), torch.float32), (4, 5, 6), torch.float32),
+                              (_FakeDev((4, 30), torch.float32), (4, 5, 6), torch.float32),
+                              (_FakeDev((4, 5, 6), torch.float32, contiguous=False), (4, 5, 6), torch.float32),
+                              (torch.zeros((4, 5, 6)), (4, 5, 6), torch.float32)]:
+        with pytest.raises(ValueError):
+            F._expect(bad, shape, dtype, "x")
+    with pytest.raises(ValueError):
+        F._expect(ok, 121, torch.float32, "x", at_least=True)

@@ -136,3 +136,30 @@ def test_concurrent_plans_on_two_streams(fd):
         torch.cuda.synchronize()
         assert torch.equal(va, ref_a) and torch.equal(vb, ref_b)
         assert pa.device_status() == 0 and pb.device_status() == 0
+
+
+def test_wrong_tensors_are_refused_before_launch(fd):
+    """Tensors of the wrong shape, dtype or layout never reach the library:
+    the binding raises ValueError and the plan stays usable."""
+    N, P, s, D = 32, 48, 1, 4
+    with fd.Plan(4.0 * N, N, N, N, P, s, D) as plan:
+        Q = torch.zeros((P, N, N), device="cuda")
+        vol = torch.empty((N, N, N), device="cuda")
+        bad = [lambda: plan.filter(torch.zeros((P, N, N - 1), device="cuda")),
+               lambda: plan.filter(torch.zeros((P, N, N), dtype=torch.float64, device="cuda")),
+               lambda: plan.backproject(torch.zeros((P - 1, N, N), device="cuda")),
+               lambda: plan.backproject(Q, torch.empty((N, N, N - 1), device="cuda")),
+               lambda: plan.backproject(Q.transpose(1, 2)),
+               lambda: plan.backproject(Q.cpu()),
+               lambda: plan.decompose(Q, torch.empty(8, device="cuda")),
+               lambda: plan.backproject_decomposed(torch.empty(8, device="cuda"), vol),
+               lambda: plan.net_backward(Q, torch.zeros(1439, device="cuda"),
+                                         torch.zeros(plan.decomposed_shape, device="cuda"), 0, N,
+                                         torch.zeros(1440, device="cuda"))]
+        for f in bad:
+            with pytest.raises(ValueError):
+                f()
+        plan.backproject(Q, vol)
+        torch.cuda.synchronize()
+        assert plan.device_status() == 0
+        assert float(vol.abs().max()) == 0.0
