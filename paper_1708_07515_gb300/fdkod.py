@@ -180,6 +180,9 @@ def fdkod_backproject_noalloc(R: float, N: int, Nu: int, Nv: int, P: int, s: int
                               stream=None) -> None:
     """FDK-OD backprojection without any allocation (scratch in the library's
     fixed device array); Q float32 [P][Nv][Nu], vol float32 [N][N][N]."""
+    import torch
+    _expect(Q, (P, Nv, Nu), torch.float32, "Q")
+    _expect(vol, (N, N, N), torch.float32, "vol")
     g = Geometry(float(R), int(N), int(Nu), int(Nv), int(P))
     _check(load().fdkod_backproject_noalloc(ctypes.byref(g), int(s), int(D), _dev_ptr(Q, "Q"), _dev_ptr(vol, "vol"),
                                             _stream(Q, stream)), "fdkod_backproject_noalloc")

@@ -156,3 +156,11 @@ def test_binding_checks_what_the_bare_pointers_cannot():
             F._expect(bad, shape, dtype, "x")
     with pytest.raises(ValueError):
         F._expect(ok, 121, torch.float32, "x", at_least=True)
+    # the allocation-free entry point knows its shapes from the geometry
+    N, P = 8, 6
+    with pytest.raises(ValueError):
+        F.fdkod_backproject_noalloc(32.0, N, N, N, P, 1, 2, _FakeDev((P, N, N + 1), torch.float32),
+                                    _FakeDev((N, N, N), torch.float32))
+    with pytest.raises(ValueError):
+        F.fdkod_backproject_noalloc(32.0, N, N, N, P, 1, 2, _FakeDev((P, N, N), torch.float32),
+                                    _FakeDev((N, N, N), torch.float16))
