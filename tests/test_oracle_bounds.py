@@ -95,3 +95,35 @@ def test_rejects_bad_arguments(oracle_mod):
         oracle_mod.bounds(100.0, 4, 4, 8, 3)     # 2^s > N
     with pytest.raises(RuntimeError):
         oracle_mod.bounds(-1.0, 16, 16, 8, 1)
+
+
+@pytest.mark.parametrize("N,s,Rf,P", [(33, 2, 1.3, 36), (256, 3, 4.0, 90), (200, 2, 1.6, 60)])
+def test_float32_positions_stay_inside_the_margins(oracle_mod, N, s, Rf, P):
+    """The one-column margins of w0 and T are there for a backprojection
+    that addresses the shifted rows in FP32: with Eq. 1, the magnification
+    and the subtraction of phi and w0 all evaluated in float32, every voxel
+    of every square still reads columns floor(t) >= 0 and floor(t) + 1 <=
+    T - 1 of its shifted row."""
+    Nu = N + 5
+    R = Rf * N
+    b = oracle_mod.bounds(R, N, Nu, P, s)
+    f = np.float32
+    beta = 2 * np.pi * np.arange(P) / P
+    cb, sb = np.cos(beta).astype(f)[:, None], np.sin(beta).astype(f)[:, None]
+    groups = _squares(N, s)
+    m = 2 ** s
+    worst_lo, worst_hi = np.inf, np.inf
+    for qy in range(m):
+        for qx in range(m):
+            q = qy * m + qx
+            X, Y = np.meshgrid(groups[qx] - (N - 1) / 2, groups[qy] - (N - 1) / 2)
+            x, y = X.ravel().astype(f)[None], Y.ravel().astype(f)[None]
+            u = f(R) * (y * cb - x * sb) / (f(R) + x * cb + y * sb) + f((Nu - 1) / 2)
+            t = u - b["phi"][q].astype(f)[:, None] - f(b["w0"][q])
+            assert t.dtype == f
+            c0 = np.floor(t)
+            assert c0.min() >= 0 and c0.max() + 1 <= b["T"][q] - 1
+            worst_lo = min(worst_lo, float(t.min()))
+            worst_hi = min(worst_hi, float(b["T"][q] - 1 - (c0.max() + 1)))
+    # the margins are not wasted: some square comes within two columns of each end
+    assert worst_lo < 2.0 and worst_hi <= 2
