@@ -150,6 +150,8 @@ FDKOD_CASES = [
     (64, 32, 2, 32, 64, 64, 4.0),      # one decimated view
     (96, 64, 1, 4, 100, 90, 4.0),      # decomposed rows of 65..128 columns (32 lanes per row)
     (96, 48, 0, 2, 96, 96, 4.0),       # rows past 128 columns (8 columns per lane)
+    (125, 144, 1, 16, 125, 125, 4.0),  # ragged 62/63-voxel squares at D = 16 (the 2000^3 square size)
+    (125, 144, 1, 24, 125, 125, 4.0),  # and at D = 24
 ]
 
 
