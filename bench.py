@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--taps", choices=["triangle", "sinc", "learned", "net"], default="triangle",
                     help="angular low-pass of the decomposition (Sec. 2.1): triangle, Hann-windowed sinc, taps "
                          "fitted to full FDK on separate training scans before the run (learn.py), or the triangle "
-                         "plus the learned residual net (tensor-core layer 2; weights from --net-weights)")
+                         "plus the learned residual net (three tensor-core layers; weights from --net-weights)")
     ap.add_argument("--net-weights", default=None,
                     help="weights of the learned decimation (.npy, 1440 values, learn_net.py --out); default: "
                          "the package's trained weights for this D if present, else seeded random weights")
