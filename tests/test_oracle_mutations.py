@@ -60,6 +60,7 @@ MUTATIONS = [
     ("representative view jD + 1", "oracle.c", "int k = j * o->D;", "int k = (j * o->D + 1) % o->P;"),
     ("no left margin in w0", "oracle.c", "int32_t w = (int32_t)floor(dmin) - 1;",
      "int32_t w = (int32_t)floor(dmin) + 1;"),
+    ("T one column short", "oracle.c", "T[q] = (int32_t)floor(dmax) + 3 - w;", "T[q] = (int32_t)floor(dmax) + 2 - w;"),
     ("squares one voxel short", "oracle.c", "*i1 = (int)((((long)q + 1) * N + m - 1) / m) - 1;",
      "*i1 = (int)((((long)q + 1) * N + m - 1) / m) - 2;"),
     ("shifted rows of the learned path with - w0", "oracle.c", SHIFT_ROWS,
