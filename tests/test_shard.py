@@ -68,7 +68,7 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_cover_the_volume_and_agree_on_time():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this multi-threaded process
     out = mgr.dict()
     mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
