@@ -36,15 +36,28 @@ sys.path.insert(0, ROOT)
 METRIC = "FDK-OD voxel-updates/s vs plain FDK on one GB300 at fixed RMSE vs FP64 oracle"
 UNIT = "voxel-updates/s"
 WORKLOAD_KEY = "fdkod_512"
-# FP32 operations per voxel update of the backprojection's inner loop:
-# row coordinate (FMA, 2), fraction (1), three lerps (sub + FMA, 3 each),
-# weighted accumulate (FMA, 2)
+# Algorithmic FP32 operations per voxel update of the backprojection, one
+# issue slot each (an FMA is one operation): row coordinate (FMA), floor,
+# fraction, three lerps (subtract + FMA each), weighted accumulate (FMA)
+OPS_PER_UPDATE = 10
+# the same work counted as FLOPs (FMA = 2) against the FMA peak
 FLOP_PER_UPDATE = 14
 # on-chip bytes per update: the four float32 samples of the bilinear gather
 SMEM_BYTES_PER_UPDATE = 16
-GB300_SMS = 152
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
+
+
+def sm_count(device=0) -> int:
+    """Streaming multiprocessors of the device the bench runs on."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def workload_config(w, qtype="f32", taps="triangle") -> dict:
+    """The workload keys both arms' JSON lines carry."""
+    return {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s, "D": w.D,
+            "q_storage": qtype, "taps": taps}
 
 
 def parse():
@@ -145,7 +158,8 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "P": w.P, "s": w.s, "D": w.D},
+        "config": {**workload_config(w), "step": "bounds + filter + decompose + backproject (FP64 oracle, "
+                                                  "one seeded slice per step)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -207,20 +221,29 @@ class Clocks:
                 "samples": len(sm)}
 
 
+TRAFFIC_PROFILE = os.path.join("profiles", "dram_traffic_fdkod_512.md")
+
+
+def kernel_text(src: str, marker: str) -> str:
+    """A kernel's source text: from its first line `marker` to the closing
+    brace at the start of a line."""
+    a = src.index(marker + "\n")
+    return src[a:src.index("\n}\n", a) + 3]
+
+
 def recorded_bp_traffic(workload: str):
     """DRAM bytes per backprojection launch from the committed ncu summary,
     or None when the summary is for another workload or the kernel's source
     text has changed since the counters were taken."""
     import hashlib
     try:
-        text = open(os.path.join(ROOT, "profiles", "dram_traffic_fdkod_512.md")).read()
-        src = open(os.path.join(ROOT, "paper_1708_07515_gb300", "csrc", "backproject.cu")).read()
-        a = src.index("template <typename TS, bool DIRECT, int WD>\n__global__")
-        b = src.index("\n}\n", a) + 3  # the kernel's closing brace
+        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
         fields = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith("bp_traffic_"))
+        src = open(os.path.join(ROOT, "paper_1708_07515_gb300", "csrc", fields["bp_traffic_source"])).read()
+        body = kernel_text(src, fields["bp_traffic_kernel_first_line"])
         if fields.get("bp_traffic_workload") != workload:
             return None
-        if fields.get("bp_traffic_kernel_sha256") != hashlib.sha256(src[a:b].encode()).hexdigest():
+        if fields.get("bp_traffic_kernel_sha256") != hashlib.sha256(body.encode()).hexdigest():
             return None
         return int(fields["bp_traffic_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
@@ -272,7 +295,7 @@ def net_roofline(w, info, T, stages, peaks):
     t = stages["decompose"] * 1e-3
     bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
     max_mhz = peaks.get("sm_max_mhz") or 2070.0
-    fp32_peak = GB300_SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    fp32_peak = sm_count() * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     return {"kernel": "net_decompose_kernel", "samples_per_launch": samples, "outputs_per_launch": outs,
             "tensor": {"bound": "tensor", "flop": mma_flop, "achieved": mma_flop / t / 1e12, "peak": bf16,
                        "unit": "TFLOP/s", "frac": mma_flop / t / 1e12 / bf16,
@@ -525,55 +548,27 @@ def main():
     torch.cuda.synchronize()
     ms_plain = max_over_ranks(a.elapsed_time(b)) / n_plain
 
-    # --- end to end through the public API with host buffers: every step
-    # uploads its projections from pinned host memory and reads its volume
-    # back; uploads and read-backs run on their own streams, double-buffered,
-    # so they overlap the neighbouring steps' compute (the plan's workspace is
-    # used by one step at a time on the compute stream)
-    if not args.no_e2e:
-        proj_h = torch.from_numpy(proj).pin_memory()
-        vol_h = [torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory() for _ in range(2)]
-        proj_dd = [proj_d, torch.empty_like(proj_d)]
-        vol_dd = [vol, torch.empty_like(vol)]
-    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
-    cst = int(stream.cuda_stream)
-
-    def e2e_run(n):
-        ev = lambda: torch.cuda.Event(enable_timing=False)
-        up, filt, comp, down = ([ev() for _ in range(n)] for _ in range(4))
-        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t_start.record(s_h2d)
-        for i in range(n):
-            b = i % 2
-            with torch.cuda.stream(s_h2d):
-                if i >= 2:
-                    s_h2d.wait_event(filt[i - 2])
-                proj_dd[b].copy_(proj_h, non_blocking=True)
-                up[i].record(s_h2d)
-            stream.wait_event(up[i])
-            plan.compute_bounds(cst)
-            plan.filter(proj_dd[b], Q, cst)
-            filt[i].record(stream)
-            if i >= 2:
-                stream.wait_event(down[i - 2])
-            plan.backproject(Q, vol_dd[b], cst)
-            comp[i].record(stream)
-            with torch.cuda.stream(s_d2h):
-                s_d2h.wait_event(comp[i])
-                vol_h[b].copy_(vol_dd[b], non_blocking=True)
-                down[i].record(s_d2h)
-        t_end.record(s_d2h)
-        torch.cuda.synchronize()
-        return t_start.elapsed_time(t_end)
-
+    # --- end to end through the library's host-buffer call (fdkod_reconstruct):
+    # every step uploads the scan's projections from page-locked host memory
+    # and reads the whole volume back into it, inside the call (uploads in
+    # view chunks overlap the filter, read-backs of z-slabs overlap the
+    # backprojection); the call is synchronous, so the host clock times it
     if args.no_e2e:
         ms_e2e, n_e2e = None, 0
     else:
-        e2e_run(max(2, min(args.warmup, 3)))
+        proj_h = torch.from_numpy(proj).pin_memory()
+        vol_h = torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory()
+        for _ in range(max(2, min(args.warmup, 3))):
+            fd.reconstruct(plan, proj_h, vol_h)
         n_e2e = max(2, min(args.steps, 10))
         barrier()
         torch.cuda.synchronize()
-        ms_e2e = max_over_ranks(e2e_run(n_e2e)) / n_e2e
+        t_e0 = time.perf_counter()
+        for _ in range(n_e2e):
+            fd.reconstruct(plan, proj_h, vol_h)
+        t_e1 = time.perf_counter()
+        ms_e2e = max_over_ranks((t_e1 - t_e0) * 1e3) / n_e2e
+        del vol_h
 
     # --- accuracy at the measured configuration, against the FP64 oracle
     extra = {}
@@ -629,9 +624,12 @@ def main():
     bp_ms = stages["backproject"]
     upd_bp = float(w.N) ** 3 * (w.P // w.D)
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_tflops = GB300_SMS * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    sms = sm_count(local)
+    ops_peak = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    ops_ach = OPS_PER_UPDATE * upd_bp / (bp_ms * 1e-3) / 1e12
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     achieved_tflops = FLOP_PER_UPDATE * upd_bp / (bp_ms * 1e-3) / 1e12
-    smem_peak = GB300_SMS * SMEM_BYTES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9
+    smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9
     smem_ach = SMEM_BYTES_PER_UPDATE * upd_bp / (bp_ms * 1e-3) / 1e9
     if rank == 0:
         out = {
@@ -641,8 +639,7 @@ def main():
             "data": ("synthetic: seeded random-ellipsoid phantom, exact cone-beam projections"
                      + (f", {100 * w.noise:g}% Gaussian noise" if w.noise else "")
                      + (" (projections generated on the GPU)" if gpu_inputs else "")),
-            "config": {"workload": w.name, "N": w.N, "P": w.P, "Nu": w.Nu, "Nv": w.Nv, "R": w.R, "s": w.s,
-                       "D": w.D, "q_storage": args.qtype, "taps": args.taps,
+            "config": {**workload_config(w, args.qtype, args.taps),
                        "step": "bounds + filter + decompose + backproject",
                        "l2": f"inputs larger than L2 (projections {proj.nbytes / 1e6:.0f} MB, decomposed data "
                              f"{info['decomposed_elems'] * 4 / 1e9:.2f} GB)",
@@ -651,16 +648,22 @@ def main():
                 "value": world * upd_eff / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": proj.nbytes, "d2h_bytes_per_step": w.N ** 3 * 4,
                 "ms_per_step": ms_e2e, "steps": n_e2e,
-                "note": "uploads and read-backs on their own streams, overlapping neighbouring steps"},
+                "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
+                "note": "host clock around whole calls; inside a call the upload (view chunks) overlaps the "
+                        "filter and the read-back (z-slabs) overlaps the backprojection"},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "alu", "kernel": "bp_tma_kernel (FDK-OD backprojection)",
-                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_tflops,
+            "roofline": {"bound": "alu", "kernel": "FDK-OD backprojection",
+                         "achieved": ops_ach, "peak": ops_peak, "unit": "TFLOP/s",
+                         "frac": ops_ach / ops_peak,
                          "traffic": recorded_bp_traffic(args.workload if args.qtype == "f32" else ""),
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                         "peak_note": f"152 SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
-                         "per_launch_updates": upd_bp, "flop_per_update": FLOP_PER_UPDATE,
+                         "peak_note": f"{sms} SMs x 128 FP32 lanes x one operation per clock x {max_mhz:.0f} MHz "
+                                      "(derived; an FMA counts one operation, as in the update's count)",
+                         "per_launch_updates": upd_bp, "flop_per_update": OPS_PER_UPDATE,
                          "avg_launch_ms": bp_ms},
+            "roofline_fma": {"achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                             "frac": achieved_tflops / peak_tflops, "flop_per_update": FLOP_PER_UPDATE,
+                             "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {max_mhz:.0f} MHz"},
             "roofline_smem": {"achieved": smem_ach, "peak": smem_peak, "unit": "GB/s", "frac": smem_ach / smem_peak,
                               "bytes_per_update": SMEM_BYTES_PER_UPDATE},
             "roofline_stages": stage_rooflines(w, info, stages, args.qtype, peaks),

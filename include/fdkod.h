@@ -256,14 +256,24 @@ int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
  * * T_stride bytes of decomposed data (T_stride ~ 1.4 N/2^s + 8) plus a few
  * KiB; larger problems return FDKOD_ERR_UNSUPPORTED without touching the
  * GPU.  Example: 128^3 from 128 views, s = 2, D = 2 needs about 30 MiB.
- * The first call on a device, with that device current, looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the array and it keeps the
- * previous call's contents: the call clears what must start at zero, but
- * calls whose work overlaps on the GPU (other streams, other host threads
- * without ordering) race on it -- order them on one stream.  Host callers
- * are serialised by a mutex.  Device-side window checks are sized out on
- * the host and are not reported by this call.
+ *
+ * First call on a device: with that device current, the call looks up the
+ * array's device address (cudaGetSymbolAddress).  With lazy module loading
+ * this is also when the driver loads the library's device code and reserves
+ * the array, which may synchronise the device, or fail with FDKOD_ERR_CUDA
+ * when the device has no room left.  Make one warm-up call per device at
+ * start-up, before any stream capture.
+ *
+ * Every call shares the array and it keeps the previous call's contents:
+ * the call clears what must start at zero, but calls whose work overlaps on
+ * the GPU (other streams, other host threads without ordering) race on it --
+ * order them on one stream.  Host callers are serialised by a mutex.  The
+ * call's tables (view cos/sin, low-pass weights) are computed on the device:
+ * it copies nothing from host memory and does not wait for the stream.
+ * Device-side checks (a staging window or a shifted-row width too small, a
+ * bounded wait that gave up) set the array's status word, which
+ * fdkod_noalloc_device_status reads; this call itself returns FDKOD_OK once
+ * the work is enqueued.
  *
  * g, s, D: as fdkod_plan; Q: device [P][Nv][Nu] float32 (already
  * filtered); vol: device [N][N][N] float32, fully overwritten; work is
@@ -272,6 +282,41 @@ int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
  */
 int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, const float *Q, float *vol,
                               uintptr_t stream);
+
+/*
+ * Device status of the most recent fdkod_backproject_noalloc call on the
+ * current device (the paper has no counterpart): waits for the work queued
+ * on `stream`, then reads and clears the status word of the fixed array
+ * (allocates nothing).  Returns FDKOD_OK, FDKOD_ERR_BOUNDS (a staging window
+ * or the host bound of the shifted-row width was too small: the volume is
+ * invalid), FDKOD_ERR_TIMEOUT (a bounded device-side wait gave up), or
+ * FDKOD_ERR_CUDA.
+ */
+int fdkod_noalloc_device_status(uintptr_t stream);
+
+/*
+ * Whole reconstruction from host buffers: the FDK filter (Sec. 1), the bound
+ * computation of Eq. 1 and the FDK-OD backprojection (Sec. 2.2) of one scan,
+ * from projections in host memory to a volume in host memory.
+ *
+ * proj_host: host [P][Nv][Nu] float32; vol_host: host [N][N][N] float32,
+ * fully overwritten.  Page-locked host memory lets the copies overlap the
+ * compute; pageable memory works, with synchronous copies.  Within the call
+ * the projections are uploaded in chunks of views and each chunk is
+ * filtered as soon as it has landed; after the decomposition the volume is
+ * backprojected in z-slabs and each slab is copied back while the next one
+ * is computed (an upload and a read-back stream of the plan's own, ordered
+ * after the work already queued on `stream`).
+ * Device memory: the first call allocates, and the plan then keeps until
+ * fdkod_destroy, buffers for the projections, the filtered projections and
+ * the volume (reported in fdkod_plan_info.device_bytes); the plan must have
+ * its decomposed-data workspace when D > 1.  Synchronous: returns once
+ * vol_host holds the volume and the device status word has been read.
+ * Calls with the same plan must not overlap.  Errors: INVALID_ARG (null
+ * pointers, a plan without a workspace and D > 1), OOM, CUDA, TIMEOUT,
+ * BOUNDS.
+ */
+int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, float *vol_host, uintptr_t stream);
 
 /*
  * Whole slab-wise reconstruction from host buffers (piecemeal FDK-OD,
@@ -409,6 +454,29 @@ void fdkod_batch_destroy(fdkod_batch_t *batch);
  */
 int fdkod_set_tile(fdkod_plan_t *plan, int window_cols);
 int fdkod_get_tile(const fdkod_plan_t *plan, int *window_cols, int *min_cols);
+
+/*
+ * Test hooks of the device-side failure paths (the paper has no
+ * counterpart; for tests of the error reporting, no GPU fault involved).
+ * They act on this plan's staged (TMA) backprojection launches only.
+ *  FDKOD_TEST_NONE: no hook (the default).
+ *  FDKOD_TEST_SKIP_COPY: the first CTA of a launch leaves out one staging
+ *    copy of its second chunk of views, so that chunk's bounded wait runs
+ *    out: the CTA records FDKOD_ERR_TIMEOUT, waits (bounded) for its other
+ *    copies in flight and exits; the other CTAs finish normally.  Needs more
+ *    than 4 backprojected views to act.
+ *  FDKOD_TEST_SMALL_WINDOW: every staged window counts as too small, so
+ *    every view is skipped (nothing is read outside a window) and
+ *    FDKOD_ERR_BOUNDS is recorded.
+ * wait_ns: limit of the bounded waits of those launches (0 = the default,
+ * 2 s), so a test does not wait seconds.  Volumes written while a hook is
+ * set are invalid.  Call while no launch of the plan is in flight.
+ * Errors: INVALID_ARG (null plan, unknown kind, negative wait_ns).
+ */
+#define FDKOD_TEST_NONE 0
+#define FDKOD_TEST_SKIP_COPY 1
+#define FDKOD_TEST_SMALL_WINDOW 2
+int fdkod_set_test_fault(fdkod_plan_t *plan, int kind, int64_t wait_ns);
 
 /* Static message for a status code. */
 const char *fdkod_strerror(int status);

@@ -133,13 +133,19 @@ def filter(proj: np.ndarray, R: float) -> np.ndarray:
     return out
 
 
-def filter_fft(proj: np.ndarray, R: float) -> np.ndarray:
+def filter_fft(proj: np.ndarray, R: float, v0: int = 0, Nv_det: int | None = None) -> np.ndarray:
     """The same filter as ``filter`` (cosine weight + linear Ram-Lak
     convolution, zero padding), computed with numpy's FP64 FFT: the kernel
     is wrapped onto a circle of length L >= 2 Nu, where every lag of the
-    linear convolution keeps its own tap.  Fast enough for full-size views."""
+    linear convolution keeps its own tap.  Fast enough for full-size views.
+    proj may hold a band of rows v0 .. v0 + proj.shape[1] - 1 of a detector
+    with Nv_det rows (default: the whole detector); rows are filtered
+    independently, each with its own cosine weight."""
     proj = np.asarray(proj)
-    P, Nv, Nu = proj.shape
+    P, nb, Nu = proj.shape
+    Nv = nb if Nv_det is None else int(Nv_det)
+    if v0 < 0 or v0 + nb > Nv:
+        raise ValueError("row band outside the detector")
     L = 1
     while L < 2 * Nu:
         L *= 2
@@ -150,9 +156,9 @@ def filter_fft(proj: np.ndarray, R: float) -> np.ndarray:
     h[odd] = -1.0 / (np.pi ** 2 * lag[odd].astype(np.float64) ** 2)
     H = np.fft.rfft(h).real
     a = np.arange(Nu) - (Nu - 1) / 2
-    b = np.arange(Nv) - (Nv - 1) / 2
+    b = np.arange(v0, v0 + nb) - (Nv - 1) / 2
     w = R / np.sqrt(R * R + a[None, :] ** 2 + b[:, None] ** 2)
-    out = np.empty((P, Nv, Nu), dtype=np.float64)
+    out = np.empty((P, nb, Nu), dtype=np.float64)
     for k in range(P):
         q = proj[k].astype(np.float64) * w
         out[k] = np.fft.irfft(np.fft.rfft(q, n=L, axis=-1) * H, n=L, axis=-1)[:, :Nu]

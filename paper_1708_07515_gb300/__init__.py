@@ -10,6 +10,9 @@ from .fdkod import (  # noqa: F401
     FDKOD_F16,
     FDKOD_F32,
     FDKOD_NET_SIZE,
+    FDKOD_TEST_NONE,
+    FDKOD_TEST_SKIP_COPY,
+    FDKOD_TEST_SMALL_WINDOW,
     BatchBackprojection,
     FdkodError,
     Plan,
@@ -25,11 +28,14 @@ from .fdkod import (  # noqa: F401
     fdkod_get_decimation_taps,
     fdkod_net_adjoint,
     fdkod_net_backward,
+    fdkod_noalloc_device_status,
     fdkod_plan,
     fdkod_set_decimation_net,
     fdkod_set_decimation_taps,
+    fdkod_set_test_fault,
     fdkod_sinc_taps,
     lib_path,
     load,
+    reconstruct,
     reconstruct_slabs,
 )

@@ -57,6 +57,8 @@ void free_plan(PlanImpl &p) {
     cudaFree(p.tapw);
     cudaFree(p.net);
     cudaFree(p.status);
+    free_host_pipe(p.pipe);
+    p.pipe = nullptr;
 }
 
 double centre(int i, int n) { return (double)i - 0.5 * (double)(n - 1); }
@@ -520,6 +522,13 @@ int fdkod_get_decimation_taps(const fdkod_plan_t *plan, double *h, int cap) {
 int fdkod_sinc_taps(int D, int H, double *h) {
     if (D < 1 || H < 1 || H > 2 || D > fdkod::kMaxTapD || !h) return FDKOD_ERR_INVALID_ARG;
     sinc_taps(D, H, h);
+    return FDKOD_OK;
+}
+
+int fdkod_set_test_fault(fdkod_plan_t *plan, int kind, int64_t wait_ns) {
+    if (!plan || kind < FDKOD_TEST_NONE || kind > FDKOD_TEST_SMALL_WINDOW || wait_ns < 0) return FDKOD_ERR_INVALID_ARG;
+    plan->impl.test_fault = kind;
+    plan->impl.wait_ns = wait_ns;
     return FDKOD_OK;
 }
 

@@ -326,6 +326,8 @@ struct BpTmaParams {
     int row0;             // detector row held in the source's row 0
     int zoff, nz;         // slices zoff .. zoff + nz - 1, written to vol[z - zoff]
     float scale;
+    unsigned long long wait_ns;  // limit of every bounded wait (ns)
+    int fault;                   // test hook (kTestFault*), 0 = none
 };
 
 // shared-memory load of one window element at a compile-time byte offset
@@ -361,6 +363,9 @@ struct Lds<__half, OFF> {
 // tbase absorbs -kMagicBits * 4 WD (keeps the unsigned arithmetic explicit)
 constexpr int kMagicBits = 0x4B400000;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
+// test hooks of the failure paths (fdkod_set_test_fault)
+constexpr int kTestFaultSkipCopy = 1;    // CTA 0 leaves out one copy of its chunk 1
+constexpr int kTestFaultSmallWindow = 2; // every window counts as too small
 
 // three CTAs per SM (the shared-memory limit): up to 80 registers per thread
 template <typename TS, bool DIRECT, int WD>
@@ -448,7 +453,8 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
                 const int xs = clo & ~(kAl - 1);  // 16-byte aligned start of the copy
                 const int vlo = (int)floorf(vmin) - 1;
                 const int vhi = (int)floorf(vmax) + 2;
-                const int skip = (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1);
+                const int skip =
+                    (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1) || a.fault == kTestFaultSmallWindow;
                 if (skip) atomicOr(a.status, 1);
                 s_pa[st][warp] = make_float4(ge.cb, ge.sb, ge.r, ge.alpha);
                 s_pb[st][warp] = make_float4(ge.gamma, ge.g_hi, toff - (float)(xs - cbase),
@@ -465,9 +471,12 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
         const int nj = min(kViewsPerStage, a.nviews - c * kViewsPerStage);
         tma::fence_proxy_async();
         tma::mbar_arrive_expect_tx(&bars[st], (uint32_t)(nj * a.RW * WD * ES));
-        for (int w = 0; w < nj; ++w)
+        for (int w = 0; w < nj; ++w) {
+            // test hook: the stage's bytes never all arrive, its wait runs out
+            if (a.fault == kTestFaultSkipCopy && c == 1 && w == 0 && blockIdx.x == 0 && blockIdx.y == 0) continue;
             tma::load_3d(sm + (size_t)(st * kViewsPerStage + w) * a.tile_stride, &tmap, &bars[st], s_tx[st][w],
                          s_ty[st][w], s_tz[st][w]);
+        }
     };
 
     if (threadIdx.x == 0) {
@@ -489,12 +498,12 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
         if (c + 1 < nch) setup(c + 1, st ^ 1);
         __syncthreads();
         if (c + 1 < nch && threadIdx.x == 0) issue(c + 1, st ^ 1);
-        const bool ok = tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+        const bool ok = tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), a.wait_ns);
         if (!__syncthreads_and(ok)) {
             // a copy never completed: report, let copies in flight land, leave
             if (threadIdx.x == 0) atomicOr(a.status, 2);
-            tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
-            if (c + 1 < nch) tma::mbar_wait_bounded(&bars[st ^ 1], (uint32_t)(((c + 1) >> 1) & 1), kWaitLimitNs);
+            tma::mbar_wait_bounded(&bars[st], (uint32_t)((c >> 1) & 1), a.wait_ns);
+            if (c + 1 < nch) tma::mbar_wait_bounded(&bars[st ^ 1], (uint32_t)(((c + 1) >> 1) & 1), a.wait_ns);
             return;
         }
         if (active) {
@@ -793,6 +802,8 @@ bool make_tma_launch(const PlanImpl &p, const SquareSet &ss, bool direct, const 
     a.row0 = b.row0;
     a.zoff = b.zoff;
     a.nz = b.nz;
+    a.wait_ns = p.wait_ns > 0 ? (unsigned long long)p.wait_ns : kWaitLimitNs;
+    a.fault = p.test_fault;
     // elements per staged window, a 128-byte multiple
     a.tile_stride = (ss.Rw * WD + (128 / es - 1)) & ~(128 / es - 1);
     if (direct) {
@@ -918,6 +929,8 @@ cudaError_t batch_create(const PlanImpl *const *plans, const void *const *src, f
         b.nz = p.g.N;
         int WD = 0;
         if (!make_tma_launch(p, p.od, direct, src[i], vols[i], b, maps[i], insts[i].a, WD)) return cudaSuccess;
+        insts[i].a.wait_ns = kWaitLimitNs;  // the persistent form has no test hooks
+        insts[i].a.fault = 0;
         insts[i].direct = direct ? 1 : 0;
         insts[i].WD = WD;
         smem = std::max(smem, sizeof(float) * (size_t)2 * kViewsPerStage * insts[i].a.tile_stride + 128);

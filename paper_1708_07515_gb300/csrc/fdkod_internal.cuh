@@ -65,6 +65,10 @@ struct __align__(16) NetWeights {
     float h[2 * kMaxTapD];
 };
 
+// Device side of the whole-volume host-buffer pipeline (slabs.cu).
+struct HostPipe;
+void free_host_pipe(HostPipe *hp);
+
 struct PlanImpl {
     fdkod_geometry g{};
     int s = 0, D = 1, Pd = 1;
@@ -94,6 +98,11 @@ struct PlanImpl {
     bool no_workspace = false; // made with FDKOD_PLAN_NO_WORKSPACE
     int *status = nullptr;     // device status word
     int64_t device_bytes = 0;
+    // test hooks of the backprojection's failure paths (fdkod_set_test_fault)
+    int test_fault = 0;
+    int64_t wait_ns = 0;       // bounded-wait limit, 0 = the kernels' default
+    // device buffers and streams of fdkod_reconstruct (made on its first call)
+    HostPipe *pipe = nullptr;
 };
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
@@ -141,7 +150,9 @@ struct Band {
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_bounds(const PlanImpl &p, SquareSet &ss, cudaStream_t st);
-cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b = Band{});
+// views: how many views proj and Q hold (default: all P)
+cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b = Band{},
+                          int views = -1);
 cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b = Band{});
 cudaError_t launch_net_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, int nrows);
 // host: refresh the device copy of the net (weights from net_host, taps from htaps)

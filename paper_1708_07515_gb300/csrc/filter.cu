@@ -285,8 +285,9 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
 }
 
 template <typename TQ>
-cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st, int row0, int rows_per_view) {
-    const long long nrows = (long long)p.g.P * rows_per_view;
+cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st, int row0, int rows_per_view,
+                     int views) {
+    const long long nrows = (long long)views * rows_per_view;
     const long long pairs = (nrows + 1) / 2;
     const int G = std::max(1, 2048 / p.L);  // 128 threads per CTA up to L = 2048
     const long long blocks = (pairs + G - 1) / G;
@@ -300,12 +301,14 @@ cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t s
 
 }  // namespace
 
-cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b) {
+cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStream_t st, Band b, int views) {
     const int rows = b.nrows < 0 ? p.g.Nv : b.nrows;
+    if (views < 0) views = p.g.P;
+    if (views == 0) return cudaSuccess;
     switch (p.qtype) {
-        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st, b.row0, rows);
-        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st, b.row0, rows);
-        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st, b.row0, rows);
+        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st, b.row0, rows, views);
+        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st, b.row0, rows, views);
+        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st, b.row0, rows, views);
     }
     return cudaErrorInvalidValue;
 }

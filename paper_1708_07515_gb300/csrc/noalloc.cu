@@ -9,10 +9,14 @@
 // and coefficients, the status word and the decomposed data S' -- lives in
 // one file-scope device array of kScratchBytes.  Every GPU that loads the
 // library holds that array until the process exits.  The caller passes Q
-// and vol, as for fdkod_backproject.
+// and vol, as for fdkod_backproject.  The call's tables are computed by a
+// kernel on the device, so it copies nothing from host memory (nothing
+// that a later call could overwrite before the copy runs, and no wait for
+// the stream's earlier work).
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "fdkod_internal.cuh"
@@ -27,9 +31,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
-double2 g_cs_host[kMaxViews];  // staging for the cos/sin upload (under g_mutex)
-double g_taps_host[fdkod::kMaxTapD];  // triangle taps and their running-sum weights (under g_mutex)
-float4 g_tapw_host[fdkod::kMaxTapD];
+double2 g_cs_host[kMaxViews];  // host cos/sin for the host-side sizing (under g_mutex)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -71,6 +73,46 @@ int max_width(const fdkod_geometry &g, int s, const double2 *cs) {
     return tmax;
 }
 
+// Per-call tables on the device: the status word (cleared), cos/sin of
+// every view (the planned path's formula, evaluated in FP64 on the device)
+// and the running-sum weights of the triangle low-pass, view j D + r adding
+// (D - r) / D^2 to decimated view j and r / D^2 to view j + 1.
+__global__ void noalloc_tables_kernel(int P, int D, double2 *cs, float4 *tapw, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *status = 0;
+    if (i < P) {
+        const double beta = 2.0 * M_PI * (double)i / (double)P;
+        cs[i] = make_double2(cos(beta), sin(beta));
+    }
+    if (i < D) {
+        const double dd = (double)D * (double)D;
+        tapw[i] = make_float4((float)((double)(D - i) / dd), i == 0 ? 0.f : (float)((double)i / dd), 0.f, 0.f);
+    }
+}
+
+// The decomposed rows are Tstride wide (a host bound); a square whose exact
+// width T (from the bound kernel) exceeds it would lose columns: report it
+// as a window overflow.
+__global__ void noalloc_width_check_kernel(const int32_t *T, int nsq, int Tstride, int *status) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsq; q += gridDim.x * blockDim.x)
+        if (T[q] > Tstride) atomicOr(status, 1);
+}
+
+// The array's device address on the current device (looked up once per
+// device, under g_mutex); null when the lookup fails.
+unsigned char *scratch_base() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (!g_scratch_addr[dev]) {
+        // host code cannot use g_scratch's name as a device address: ask the
+        // runtime for this device's copy, once, with the device current
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return nullptr;
+        g_scratch_addr[dev] = ptr;
+    }
+    return (unsigned char *)g_scratch_addr[dev];
+}
+
 }  // namespace
 
 extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, const float *Q, float *vol,
@@ -83,16 +125,8 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
     if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;
 
     std::lock_guard<std::mutex> lock(g_mutex);
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDKOD_ERR_CUDA;
-    if (!g_scratch_addr[dev]) {
-        // host code cannot use g_scratch's name as a device address: ask the
-        // runtime for this device's copy, once, with the device current
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return FDKOD_ERR_CUDA;
-        g_scratch_addr[dev] = ptr;
-    }
-    unsigned char *base = (unsigned char *)g_scratch_addr[dev];
+    unsigned char *base = scratch_base();
+    if (!base) return FDKOD_ERR_CUDA;
 
     PlanImpl p;
     p.g = *g;
@@ -120,7 +154,7 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
         off = align256(off + bytes);
         return ptr;
     };
-    p.status = (int *)take(sizeof(int));
+    p.status = (int *)take(sizeof(int));  // first: fdkod_noalloc_device_status reads it here
     p.cs = (double2 *)take(sizeof(double2) * g->P);
     ss.lo = (int32_t *)take(sizeof(int32_t) * n);
     ss.hi = (int32_t *)take(sizeof(int32_t) * n);
@@ -135,18 +169,31 @@ extern "C" int fdkod_backproject_noalloc(const fdkod_geometry *g, int s, int D, 
     size_windows(p, ss, g_cs_host);
 
     cudaStream_t st = (cudaStream_t)stream;
-    // the array keeps the previous call's contents: clear the status word;
-    // every other region is fully rewritten below before it is read
-    if (cudaMemsetAsync(p.status, 0, sizeof(int), st) != cudaSuccess) return FDKOD_ERR_CUDA;
-    if (cudaMemcpyAsync(p.cs, g_cs_host, sizeof(double2) * g->P, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return FDKOD_ERR_CUDA;
-    // the default (triangle) angular low-pass
-    triangle_taps(D, g_taps_host);
-    tap_table(g_taps_host, 1, D, g_tapw_host);
-    if (cudaMemcpyAsync(p.tapw, g_tapw_host, sizeof(float4) * D, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return FDKOD_ERR_CUDA;
+    // the array keeps the previous call's contents: the table kernel clears
+    // the status word; every other region is fully rewritten below before it
+    // is read
+    const int nt = std::max(g->P, D);
+    noalloc_tables_kernel<<<(nt + 255) / 256, 256, 0, st>>>(g->P, D, p.cs, p.tapw, p.status);
+    if (cudaGetLastError() != cudaSuccess) return FDKOD_ERR_CUDA;
     if (launch_bounds(p, ss, st) != cudaSuccess) return FDKOD_ERR_CUDA;
     if (D == 1) return launch_backproject(p, ss, true, Q, vol, st) == cudaSuccess ? FDKOD_OK : FDKOD_ERR_CUDA;
+    noalloc_width_check_kernel<<<1, 256, 0, st>>>(ss.T, ss.nsq, p.Tstride, p.status);
+    if (cudaGetLastError() != cudaSuccess) return FDKOD_ERR_CUDA;
     if (launch_decompose(p, Q, p.Sp, st) != cudaSuccess) return FDKOD_ERR_CUDA;
     return launch_backproject(p, ss, false, p.Sp, vol, st) == cudaSuccess ? FDKOD_OK : FDKOD_ERR_CUDA;
+}
+
+extern "C" int fdkod_noalloc_device_status(uintptr_t stream) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    unsigned char *base = scratch_base();
+    if (!base) return FDKOD_ERR_CUDA;
+    int *status = (int *)base;  // the first region of every call's layout
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return FDKOD_ERR_CUDA;
+    if (h & 2) return FDKOD_ERR_TIMEOUT;
+    if (h & 1) return FDKOD_ERR_BOUNDS;
+    return FDKOD_OK;
 }

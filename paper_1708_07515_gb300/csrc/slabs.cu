@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "fdkod_internal.cuh"
@@ -125,6 +126,146 @@ extern "C" int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_hos
         SLAB_TRY(cudaEventRecord(ev_down[i], r.down));
     }
     SLAB_TRY(cudaStreamSynchronize(r.down));
+    SLAB_TRY(cudaStreamSynchronize(comp));
+    return fdkod_last_device_status(plan, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Whole-volume reconstruction from host buffers (fdkod_reconstruct): the
+// plan keeps device buffers for the projections, the filtered projections
+// and the volume, plus an upload and a read-back stream (made on the first
+// call).  Within one call
+//   - the projections go up in chunks of views on the upload stream, and
+//     the compute stream filters each chunk as soon as it has landed;
+//   - the bounds, the decomposition and the backprojection run on the
+//     compute stream once every view is filtered;
+//   - the backprojection runs in z-slabs, and each slab's read-back on the
+//     read-back stream overlaps the next slab's backprojection.
+namespace fdkod {
+
+constexpr int kPipeChunks = 8;  // view chunks of the upload
+constexpr int kPipeSlabs = 4;   // z-slabs of the backprojection / read-back
+
+struct HostPipe {
+    float *proj = nullptr, *vol = nullptr;
+    void *Q = nullptr;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_up[kPipeChunks] = {}, ev_slab[kPipeSlabs] = {}, ev_start = nullptr;
+    int64_t bytes = 0;
+};
+
+void free_host_pipe(HostPipe *hp) {
+    if (!hp) return;
+    if (hp->up) cudaStreamSynchronize(hp->up);
+    if (hp->down) cudaStreamSynchronize(hp->down);
+    for (cudaEvent_t e : hp->ev_up)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : hp->ev_slab)
+        if (e) cudaEventDestroy(e);
+    if (hp->ev_start) cudaEventDestroy(hp->ev_start);
+    if (hp->up) cudaStreamDestroy(hp->up);
+    if (hp->down) cudaStreamDestroy(hp->down);
+    cudaFree(hp->proj);
+    cudaFree(hp->Q);
+    cudaFree(hp->vol);
+    delete hp;
+}
+
+}  // namespace fdkod
+
+namespace {
+
+cudaError_t make_pipe(PlanImpl &p, fdkod::HostPipe **out) {
+    using fdkod::HostPipe;
+    HostPipe *hp = new (std::nothrow) HostPipe;
+    if (!hp) return cudaErrorMemoryAllocation;
+    const size_t samples = (size_t)p.g.P * p.g.Nv * p.g.Nu;
+    const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
+    const size_t voxels = (size_t)p.g.N * p.g.N * p.g.N;
+    cudaError_t e;
+    if ((e = cudaMalloc(&hp->proj, sizeof(float) * samples)) != cudaSuccess ||
+        (e = cudaMalloc(&hp->Q, es * samples)) != cudaSuccess ||
+        (e = cudaMalloc(&hp->vol, sizeof(float) * voxels)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&hp->up, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&hp->down, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&hp->ev_start, cudaEventDisableTiming)) != cudaSuccess) {
+        fdkod::free_host_pipe(hp);
+        return e;
+    }
+    for (auto &ev : hp->ev_up)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            fdkod::free_host_pipe(hp);
+            return e;
+        }
+    for (auto &ev : hp->ev_slab)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            fdkod::free_host_pipe(hp);
+            return e;
+        }
+    hp->bytes = (int64_t)(sizeof(float) * samples + es * samples + sizeof(float) * voxels);
+    *out = hp;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, float *vol_host, uintptr_t stream) {
+    using fdkod::kPipeChunks;
+    using fdkod::kPipeSlabs;
+    if (!plan || !proj_host || !vol_host) return FDKOD_ERR_INVALID_ARG;
+    PlanImpl &p = plan->impl;
+    if (p.D > 1 && !p.Sp) return FDKOD_ERR_INVALID_ARG;  // plan made without a workspace
+    if (!p.pipe) {
+        fdkod::HostPipe *hp = nullptr;
+        SLAB_TRY(make_pipe(p, &hp));
+        p.pipe = hp;
+        p.device_bytes += hp->bytes;
+    }
+    fdkod::HostPipe &hp = *p.pipe;
+    const int N = p.g.N, Nv = p.g.Nv, Nu = p.g.Nu, P = p.g.P;
+    const size_t view = (size_t)Nv * Nu;
+    const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
+    cudaStream_t comp = (cudaStream_t)stream;
+    // the previous call's work on the compute stream (and the caller's) comes first
+    SLAB_TRY(cudaEventRecord(hp.ev_start, comp));
+    SLAB_TRY(cudaStreamWaitEvent(hp.up, hp.ev_start, 0));
+    // upload in chunks of an even number of views (the filter pairs rows in
+    // one complex transform; even chunk starts keep the whole-array pairing)
+    int cv = (P + kPipeChunks - 1) / kPipeChunks;
+    cv += cv & 1;
+    int nch = 0;
+    for (int k0 = 0; k0 < P; k0 += cv, ++nch) {
+        const int nv = std::min(cv, P - k0);
+        SLAB_TRY(cudaMemcpyAsync(hp.proj + (size_t)k0 * view, proj_host + (size_t)k0 * view,
+                                 sizeof(float) * view * nv, cudaMemcpyHostToDevice, hp.up));
+        SLAB_TRY(cudaEventRecord(hp.ev_up[nch], hp.up));
+    }
+    SLAB_TRY(fdkod::launch_bounds(p, p.od, comp));
+    nch = 0;
+    for (int k0 = 0; k0 < P; k0 += cv, ++nch) {
+        const int nv = std::min(cv, P - k0);
+        SLAB_TRY(cudaStreamWaitEvent(comp, hp.ev_up[nch], 0));
+        SLAB_TRY(fdkod::launch_filter(p, hp.proj + (size_t)k0 * view, (char *)hp.Q + es * (size_t)k0 * view, comp,
+                                      fdkod::Band{}, nv));
+    }
+    if (p.D > 1) SLAB_TRY(fdkod::launch_decompose(p, hp.Q, p.Sp, comp));
+    // backprojection in z-slabs of whole 32-slice tiles; read-back overlapped
+    int zs = (N + kPipeSlabs - 1) / kPipeSlabs;
+    zs = (zs + fdkod::kZT - 1) / fdkod::kZT * fdkod::kZT;
+    int ns = 0;
+    for (int z0 = 0; z0 < N; z0 += zs, ++ns) {
+        fdkod::Band b;
+        b.zoff = z0;
+        b.nz = std::min(zs, N - z0);
+        float *dst = hp.vol + (size_t)z0 * N * N;
+        if (p.D == 1) SLAB_TRY(fdkod::launch_backproject(p, p.od, true, hp.Q, dst, comp, b));
+        else SLAB_TRY(fdkod::launch_backproject(p, p.od, false, p.Sp, dst, comp, b));
+        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], comp));
+        SLAB_TRY(cudaStreamWaitEvent(hp.down, hp.ev_slab[ns], 0));
+        SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)z0 * N * N, dst, sizeof(float) * (size_t)b.nz * N * N,
+                                 cudaMemcpyDeviceToHost, hp.down));
+    }
+    SLAB_TRY(cudaStreamSynchronize(hp.down));
     SLAB_TRY(cudaStreamSynchronize(comp));
     return fdkod_last_device_status(plan, stream);
 }

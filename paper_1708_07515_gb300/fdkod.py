@@ -67,6 +67,8 @@ def load():
                 "fdkod_backproject_decomposed": (i, [vp, vp, vp, u]),
                 "fdkod_compute_bounds": (i, [vp, u]),
                 "fdkod_backproject_noalloc": (i, [ctypes.POINTER(Geometry), i, i, vp, vp, u]),
+                "fdkod_noalloc_device_status": (i, [u]),
+                "fdkod_set_test_fault": (i, [vp, i, ctypes.c_int64]),
                 "fdkod_get_bounds": (i, [vp, vp, vp, vp, vp, vp, vp]),
                 "fdkod_last_device_status": (i, [vp, u]),
                 "fdkod_strerror": (ctypes.c_char_p, [i]),
@@ -74,6 +76,7 @@ def load():
                 "fdkod_get_decimation_taps": (i, [vp, vp, i]),
                 "fdkod_sinc_taps": (i, [i, i, vp]),
                 "fdkod_reconstruct_slabs": (i, [vp, vp, vp, i, u, ctypes.POINTER(ctypes.c_int64)]),
+                "fdkod_reconstruct": (i, [vp, vp, vp, u]),
                 "fdkod_set_decimation_net": (i, [vp, vp, i]),
                 "fdkod_get_decimation_net": (i, [vp, vp, i]),
                 "fdkod_net_adjoint": (i, [vp, vp, vp, i, vp, vp, u]),
@@ -186,6 +189,23 @@ def fdkod_backproject_noalloc(R: float, N: int, Nu: int, Nv: int, P: int, s: int
     g = Geometry(float(R), int(N), int(Nu), int(Nv), int(P))
     _check(load().fdkod_backproject_noalloc(ctypes.byref(g), int(s), int(D), _dev_ptr(Q, "Q"), _dev_ptr(vol, "vol"),
                                             _stream(Q, stream)), "fdkod_backproject_noalloc")
+
+
+def fdkod_noalloc_device_status(stream=None) -> int:
+    """Status of the last fdkod_backproject_noalloc call on the current
+    device (read and cleared after the stream's work): 0, -5 (a bounded wait
+    gave up) or -6 (a window or the shifted-row width bound was too small)."""
+    import torch
+    st = int(torch.cuda.current_stream().cuda_stream) if stream is None else int(stream)
+    return int(load().fdkod_noalloc_device_status(st))
+
+
+FDKOD_TEST_NONE, FDKOD_TEST_SKIP_COPY, FDKOD_TEST_SMALL_WINDOW = 0, 1, 2
+
+
+def fdkod_set_test_fault(plan: int, kind: int, wait_ns: int = 0) -> None:
+    """Test hook of the backprojection's failure paths (see include/fdkod.h)."""
+    _check(load().fdkod_set_test_fault(plan, int(kind), int(wait_ns)), "fdkod_set_test_fault")
 
 
 def fdkod_get_bounds(plan: int, n_squares: int, P: int) -> dict:
@@ -505,6 +525,39 @@ class Plan:
         import torch
         st = int(torch.cuda.current_stream().cuda_stream) if stream is None else int(stream)
         return int(load().fdkod_last_device_status(self.handle, st))
+
+
+def _host_ptr(a, what, shape):
+    """Pointer of a C-contiguous float32 host array (numpy or torch CPU
+    tensor) of the given shape; ValueError otherwise."""
+    if hasattr(a, "data_ptr"):   # torch CPU tensor
+        if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float32" or tuple(a.shape) != shape:
+            raise ValueError(f"{what} must be a contiguous float32 CPU tensor of shape {shape}")
+        return ctypes.c_void_p(a.data_ptr())
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"] or a.shape != shape:
+        raise ValueError(f"{what} must be a C-contiguous float32 array of shape {shape}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def reconstruct(plan: Plan, proj_host, out=None, stream=None):
+    """One whole reconstruction from host memory through fdkod_reconstruct:
+    filter, bounds, FDK-OD backprojection, with the upload of the
+    projections (in chunks of views) and the read-back of the volume (in
+    z-slabs) overlapping the compute.  proj_host: float32 [P][Nv][Nu]
+    (numpy or torch CPU; page-locked memory lets the copies overlap); returns
+    the float32 [N][N][N] volume (numpy, or `out`, numpy or torch CPU)."""
+    N = plan.N
+    if not hasattr(proj_host, "data_ptr"):
+        proj_host = np.ascontiguousarray(proj_host, dtype=np.float32)
+    if out is None:
+        out = np.empty((N, N, N), dtype=np.float32)
+    src = _host_ptr(proj_host, "proj_host", (plan.P, plan.Nv, plan.Nu))
+    dst = _host_ptr(out, "out", (N, N, N))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().fdkod_reconstruct(plan.handle, src, dst, int(stream)), "fdkod_reconstruct")
+    return out
 
 
 def reconstruct_slabs(plan: Plan, proj_host, slab: int, out=None, stream=None):

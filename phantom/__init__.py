@@ -95,6 +95,11 @@ def _load():
                 fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ptr)]
+            fn = lib.phantom_project_band_f32
+            fn.restype = ctypes.c_int
+            fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int,
+                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_float)]
             _lib = lib
     return _lib
 
@@ -143,14 +148,26 @@ def make_phantom(seed: int, N: int, n_ell: int) -> np.ndarray:
 
 
 def project(ell: np.ndarray, R: float, Nu: int, Nv: int, P: int, k0: int = 0, k1: int | None = None,
-            dtype=np.float32) -> np.ndarray:
-    """Exact line integrals, array [k1-k0][Nv][Nu] of dtype float32 or float64."""
+            dtype=np.float32, rows: tuple[int, int] | None = None) -> np.ndarray:
+    """Exact line integrals, array [k1-k0][Nv][Nu] of dtype float32 or float64;
+    with rows = (v0, v1) only detector rows v0..v1-1, [k1-k0][v1-v0][Nu]
+    (float32)."""
     lib = _load()
     k1 = P if k1 is None else k1
     ell = np.ascontiguousarray(ell, dtype=np.float64).reshape(-1, NPAR)
     n = ell.shape[0]
-    out = np.empty((k1 - k0, Nv, Nu), dtype=dtype)
     ep = ell.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if rows is not None:
+        if dtype != np.float32:
+            raise ValueError("row bands are float32")
+        v0, v1 = int(rows[0]), int(rows[1])
+        out = np.empty((k1 - k0, max(0, v1 - v0), Nu), dtype=np.float32)
+        rc = lib.phantom_project_band_f32(n, ep, R, Nu, Nv, P, k0, k1, v0, v1,
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc != 0:
+            raise RuntimeError(f"phantom projector failed ({rc})")
+        return out
+    out = np.empty((k1 - k0, Nv, Nu), dtype=dtype)
     if dtype == np.float64:
         rc = lib.phantom_project_f64(n, ep, R, Nu, Nv, P, k0, k1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     elif dtype == np.float32:

@@ -117,6 +117,34 @@ int phantom_project_f64(int n_ell, const double *ell, double R, int Nu, int Nv,
     return 0;
 }
 
+/* Detector rows v0..v1-1 only, for angles k0..k1-1, rounded to float32:
+ * out[(k-k0)][v-v0][u] (the rows a bounded sample of slices reads). */
+int phantom_project_band_f32(int n_ell, const double *ell, double R, int Nu, int Nv, int P, int k0, int k1,
+                             int v0, int v1, float *out) {
+    if (bad_args(n_ell, Nu, Nv, P, k0, k1) || v0 < 0 || v1 > Nv || v0 > v1) return -1;
+    const int nb = v1 - v0;
+    long rows = (long)(k1 - k0) * nb;
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *acc = (double *)malloc(sizeof(double) * (size_t)Nu);
+        if (!acc) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (long r = 0; r < rows; ++r) {
+            if (!acc) continue;
+            int kk = (int)(r / nb), v = v0 + (int)(r % nb);
+            project_row(n_ell, ell, R, Nu, Nv, P, k0 + kk, v, acc);
+            float *row = out + (size_t)r * Nu;
+            for (int u = 0; u < Nu; ++u) row[u] = (float)acc[u];
+        }
+        free(acc);
+    }
+    return fail ? -2 : 0;
+}
+
 /* Same, rounded to float32 (the pipeline's input precision). */
 int phantom_project_f32(int n_ell, const double *ell, double R, int Nu, int Nv,
                         int P, int k0, int k1, float *out) {

@@ -64,6 +64,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.fdkod_set_tile(None, 0) == -1
     assert lib.fdkod_get_tile(None, None, None) == -1
     assert lib.fdkod_batch_backproject(None, 0) == -1
+    assert lib.fdkod_reconstruct(None, None, None, 0) == -1
+    assert lib.fdkod_set_test_fault(None, 0, 0) == -1
     lib.fdkod_batch_destroy(None)
     for rc in (0, -1, -2, -3, -4, -5, -6, 99):
         assert lib.fdkod_strerror(rc)

@@ -7,31 +7,55 @@ import shutil
 import bench
 
 
-def test_traffic_record_applies_to_its_own_workload_only():
-    got = bench.recorded_bp_traffic("fdkod_512")
-    assert isinstance(got, int) and got > 0
+KERNEL_LINE = "template <typename TS, bool DIRECT, int WD>"
+
+
+def _tree(tmp_path, monkeypatch, src, workload="fdkod_512"):
+    """A copy of the two files the record reads, with a record whose hash
+    matches the kernel text of `src` (as a fresh capture would write it)."""
+    import hashlib
+    os.makedirs(tmp_path / "profiles", exist_ok=True)
+    os.makedirs(tmp_path / "paper_1708_07515_gb300" / "csrc", exist_ok=True)
+    dst = tmp_path / "paper_1708_07515_gb300" / "csrc" / "backproject.cu"
+    dst.write_text(src)
+    sha = hashlib.sha256(bench.kernel_text(src, KERNEL_LINE).encode()).hexdigest()
+    (tmp_path / bench.TRAFFIC_PROFILE).write_text(
+        "# summary\n\nbp_traffic_bytes_per_launch: 123456\n"
+        f"bp_traffic_workload: {workload}\nbp_traffic_source: backproject.cu\n"
+        f"bp_traffic_kernel_first_line: {KERNEL_LINE}\nbp_traffic_kernel_sha256: {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return dst
+
+
+def _src():
+    return open(os.path.join(bench.ROOT, "paper_1708_07515_gb300", "csrc", "backproject.cu")).read()
+
+
+def test_committed_record_names_its_kernel():
+    text = open(os.path.join(bench.ROOT, bench.TRAFFIC_PROFILE)).read()
+    fields = dict(l.split(": ", 1) for l in text.splitlines() if l.startswith("bp_traffic_"))
+    src = open(os.path.join(bench.ROOT, "paper_1708_07515_gb300", "csrc", fields["bp_traffic_source"])).read()
+    assert bench.kernel_text(src, fields["bp_traffic_kernel_first_line"])
+    assert int(fields["bp_traffic_bytes_per_launch"]) > 0
+
+
+def test_traffic_record_applies_to_its_own_workload_only(tmp_path, monkeypatch):
+    _tree(tmp_path, monkeypatch, _src())
+    assert bench.recorded_bp_traffic("fdkod_512") == 123456
     assert bench.recorded_bp_traffic("fdkod_1024") is None
 
 
 def test_traffic_record_is_dropped_once_the_kernel_text_changes(tmp_path, monkeypatch):
-    root = bench.ROOT
-    os.makedirs(tmp_path / "profiles")
-    os.makedirs(tmp_path / "paper_1708_07515_gb300" / "csrc")
-    shutil.copy(os.path.join(root, "profiles", "dram_traffic_fdkod_512.md"), tmp_path / "profiles")
-    src = open(os.path.join(root, "paper_1708_07515_gb300", "csrc", "backproject.cu")).read()
-    dst = tmp_path / "paper_1708_07515_gb300" / "csrc" / "backproject.cu"
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    dst.write_text(src)
+    src = _src()
+    dst = _tree(tmp_path, monkeypatch, src)
     assert bench.recorded_bp_traffic("fdkod_512") is not None
     # text outside the kernel may change
     dst.write_text(src + "\n// trailing comment\n")
     assert bench.recorded_bp_traffic("fdkod_512") is not None
     # one changed statement inside it may not
-    i = src.index("template <typename TS, bool DIRECT, int WD>\n__global__")
-    j = src.index("\n}\n", i)
-    body = src[i:j]
+    body = bench.kernel_text(src, KERNEL_LINE)
     assert "acc[i] * a.scale" in body
-    dst.write_text(src[:i] + body.replace("acc[i] * a.scale", "acc[i] * a.scale * 1.0f", 1) + src[j:])
+    dst.write_text(src.replace(body, body.replace("acc[i] * a.scale", "acc[i] * a.scale * 1.0f", 1)))
     assert bench.recorded_bp_traffic("fdkod_512") is None
 
 

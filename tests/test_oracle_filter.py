@@ -86,3 +86,17 @@ def test_fft_form_equals_direct_convolution(oracle_mod, Nu, Nv):
     a = oracle_mod.filter(proj, R)
     b = oracle_mod.filter_fft(proj, R)
     np.testing.assert_allclose(b, a, rtol=0, atol=1e-12 * np.abs(proj).max())
+
+
+def test_fft_form_on_a_row_band_equals_the_direct_rows(oracle_mod):
+    """A band of rows filtered on its own (each row with its own cosine
+    weight b = v - (Nv-1)/2) equals the direct convolution of those rows of
+    the whole detector."""
+    rng = np.random.default_rng(31)
+    P, Nv, Nu, R = 3, 40, 37, 90.0
+    proj = rng.standard_normal((P, Nv, Nu)).astype(np.float32)
+    v0, v1 = 11, 29
+    band = oracle_mod.filter_fft(proj[:, v0:v1], R, v0=v0, Nv_det=Nv)
+    np.testing.assert_allclose(band, oracle_mod.filter(proj, R)[:, v0:v1], rtol=0, atol=1e-12)
+    with pytest.raises(ValueError):
+        oracle_mod.filter_fft(proj[:, v0:v1], R, v0=30, Nv_det=Nv)

@@ -84,3 +84,14 @@ def test_phantom_recipe_is_seeded():
     for e in a:
         q = e[6:15].reshape(3, 3)
         np.testing.assert_allclose(q @ q.T, np.eye(3), atol=1e-12)
+
+
+def test_row_band_equals_the_rows_of_the_whole_detector():
+    """The band projector evaluates the same rays as the whole-detector one."""
+    ell = phantom.make_phantom(91, 24, 5)
+    R = 80.0
+    full = phantom.project(ell, R, 30, 26, 7)
+    band = phantom.project(ell, R, 30, 26, 7, rows=(9, 17))
+    assert band.shape == (7, 8, 30)
+    assert np.array_equal(band, full[:, 9:17])
+    assert phantom.project(ell, R, 30, 26, 7, k0=2, k1=5, rows=(0, 26)).shape == (3, 26, 30)

@@ -36,7 +36,7 @@ def _case(oracle_mod, N, P, seed):
 
 def _close(got, want):
     g = got.double()
-    w = want.double()
+    w = want.double().to(g.device)
     rel = float(torch.linalg.norm(g - w) / torch.linalg.norm(w))
     mx = float((g - w).abs().max() / w.abs().max())
     assert rel <= REL_RMSE and mx <= MAX_REL, (rel, mx)
@@ -57,8 +57,23 @@ def test_noalloc_matches_planned_backprojection(fd, oracle_mod):
         R, N, P, s, D, Q, want = refs[i]
         vol = torch.full((N, N, N), float("nan"), device="cuda")
         fd.fdkod_backproject_noalloc(R, N, N, N, P, s, D, Q, vol)
-        torch.cuda.synchronize()
+        assert fd.fdkod_noalloc_device_status() == 0
         _close(vol, want)
+
+
+@pytest.mark.parametrize("N,P,s,D,Rf", [(64, 96, 3, 4, 4.0), (48, 60, 2, 3, 1.3), (40, 32, 1, 2, 0.9),
+                                        (33, 48, 3, 6, 2.0), (96, 72, 2, 8, 4.0)])
+def test_noalloc_matches_the_oracle(fd, oracle_mod, N, P, s, D, Rf):
+    """Directly against the FP64 oracle's FDK-OD, over decomposition levels,
+    ragged squares and short source distances; the status word also says
+    the host bound of the shifted-row width held (FDKOD_OK, not BOUNDS)."""
+    R = max(Rf * N, np.sqrt(2.0) * N / 2 + 1.5)
+    p = phantom.project(phantom.make_phantom(3100 + N, N, 8), R, N, N, P)
+    Q = oracle_mod.filter(p, R).astype(np.float32)
+    vol = torch.full((N, N, N), float("nan"), device="cuda")
+    fd.fdkod_backproject_noalloc(R, N, N, N, P, s, D, torch.from_numpy(Q).cuda(), vol)
+    assert fd.fdkod_noalloc_device_status() == 0
+    _close(vol, torch.from_numpy(oracle_mod.fdkod(Q, R, N, s, D)).cuda())
 
 
 def test_noalloc_rejects_problems_over_its_fixed_memory(fd):
