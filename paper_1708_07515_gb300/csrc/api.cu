@@ -53,6 +53,7 @@ void free_plan(PlanImpl &p) {
     cudaFree(p.cs);
     cudaFree(p.H);
     cudaFree(p.tw);
+    cudaFree(p.tw2);
     cudaFree(p.Sp);
     cudaFree(p.tapw);
     cudaFree(p.net);
@@ -81,7 +82,7 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     const int N = p.g.N, P = p.g.P;
     const int mside = (N + ss.m - 1) / ss.m;
     ss.tiles_per_side = (mside + kTile - 1) / kTile;
-    double ext_t = 0.0, ext_v = 0.0;
+    double ext_t = 0.0, ext_v = 0.0, ext_v2 = 0.0;
     // the last slab's tile may run kZT slices past the volume
     const double zabs = 0.5 * (double)(N - 1) + kZT;
     for (int q = 0; q < ss.nsq; ++q) {
@@ -110,6 +111,7 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
                         }
                     ext_t = std::max(ext_t, tmax - tmin);
                     ext_v = std::max(ext_v, (double)(kZT - 1) * umax + zabs * (umax - umin));
+                    ext_v2 = std::max(ext_v2, (double)(kZP - 1) * umax + zabs * (umax - umin));
                 }
             }
     }
@@ -118,6 +120,7 @@ void size_windows(const PlanImpl &p, SquareSet &ss, const double2 *cs) {
     ss.Wd = (int)ceil(ext_t) + 5;
     ss.Wd += ss.Wd & 1;  // even width: odd shared-memory row stride
     ss.Rw = (int)ceil(ext_v) + 5;
+    ss.Rw2 = (int)ceil(ext_v2) + 5;
     // TMA copies start on a 16-byte boundary: up to 3 more float32 columns,
     // or 7 more 16-bit columns
     const int need = (int)ceil(ext_t) + 8, need16 = (int)ceil(ext_t) + 12;
@@ -223,6 +226,17 @@ int make_fft_tables(PlanImpl &p, cudaStream_t st) {
     FDKOD_TRY(dalloc(p, &p.tw, (size_t)L));
     FDKOD_TRY(cudaMemcpyAsync(p.H, H.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
     FDKOD_TRY(cudaMemcpyAsync(p.tw, tw.data(), sizeof(float2) * L, cudaMemcpyHostToDevice, st));
+    std::vector<float2> tw2;
+    if (L == 1024) {  // the warp transform's twiddles W^(a b), a, b < 32
+        tw2.resize(1024);
+        for (int a = 0; a < 32; ++a)
+            for (int b = 0; b < 32; ++b) {
+                const double ang = 2.0 * M_PI * (double)(a * b) / 1024.0;
+                tw2[(size_t)a * 32 + b] = make_float2((float)cos(ang), (float)(-sin(ang)));
+            }
+        FDKOD_TRY(dalloc(p, &p.tw2, tw2.size()));
+        FDKOD_TRY(cudaMemcpyAsync(p.tw2, tw2.data(), sizeof(float2) * tw2.size(), cudaMemcpyHostToDevice, st));
+    }
     FDKOD_TRY(cudaStreamSynchronize(st));
     return FDKOD_OK;
 }

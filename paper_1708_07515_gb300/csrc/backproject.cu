@@ -547,6 +547,296 @@ bp_tma_kernel(const __grid_constant__ CUtensorMap tmap, BpTmaParams a) {
 }
 
 // ---------------------------------------------------------------------------
+// Mirrored-pair form of the staged backprojection (whole volumes).  Each
+// thread owns kZP slices p0 .. p0 + kZP - 1 of the lower half of its (x, y)
+// column and their mirror images N - 1 - p about the mid-plane z = 0.  A
+// voxel and its mirror read the same column (Eq. 1 does not involve z) and
+// mirrored rows: z/U + (Nv-1)/2 and -z/U + (Nv-1)/2 add up to Nv - 1.  So
+// the column weights, the row fraction and the per-view set-up are shared
+// by the pair, and with the two windows of a view staged at row origins vlo
+// and vlo', the mirror's window row is C - v for C = Nv - 1 - vlo - vlo'.
+// Row coordinates are 9.23 fixed point: v = V 2^-23 advances by an integer
+// step per slice, the row is V >> 23 and the fraction's float is the
+// mantissa bits of V under the exponent of 1.0.  Where every thread of a
+// warp has 1/U <= 1 for the view, consecutive slices move by 0 or 1 row,
+// so each slice loads only its new row of the pair (two samples per voxel
+// instead of four) and keeps the other from the previous slice.
+struct BpPairParams {
+    float *vol;
+    const GeomEntry *geo;
+    const int32_t *crop;
+    const int32_t *w0;
+    int *status;
+    int N, P, Nv, m, tps;
+    int nviews, vstep, Pd;
+    int RW, tile_stride;  // rows of a kZP-slice window; elements per staged window
+    int pbase, pend;      // slice pairs pbase .. pend - 1 (pair p: slices p and N - 1 - p)
+    float scale;
+    unsigned long long wait_ns;
+    int fault;
+};
+
+// Warp-specialised: warp 8 is the producer (per chunk of VPS views it finds
+// the windows, writes the view parameters and issues the copies into a ring
+// of kPairSlots slots); warps 0-7 consume.  A slot is full when its copies
+// have landed (full[slot], which also publishes the producer's parameters)
+// and free again when all eight consumer warps have arrived on empty[slot]:
+// no block-wide barrier inside the view loop, so consumer warps drift within
+// the ring instead of waiting for the slowest.  Every wait is bounded
+// (FDKOD_ERR_TIMEOUT); a producer that gives up waits for its copies in
+// flight before it leaves.  The producer polls `empty` (mbarrier.test_wait):
+// suspended in mbarrier.try_wait it was measured to resume late (the whole
+// kernel 1.4x slower); the consumers' waits on `full` are mostly satisfied
+// at once and suspend (polling them measured no faster).
+constexpr int kPairSlots = 3;
+constexpr int kPairConsumers = kThreads / 32;      // 8
+constexpr int kPairThreads = kThreads + 32;        // plus the producer warp
+
+template <typename TS, bool DIRECT, int WD, int VPS>
+__global__ void __launch_bounds__(kPairThreads, 3)
+bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
+    constexpr int ES = (int)sizeof(TS);
+    constexpr int kAl = 16 / ES;
+    constexpr uint32_t ROWB = (uint32_t)(ES * WD);  // bytes per window row
+    constexpr float kFix = 8388608.0f;              // 2^23
+    static_assert(VPS * 16 <= 32, "the producer warp sets up VPS views at 16 lanes each");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TS *sm = (TS *)(smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u));
+    const uint32_t sbase = tma::smem_u32(sm);
+    __shared__ __align__(8) uint64_t full[kPairSlots], empty[kPairSlots];
+    __shared__ float4 s_pa[kPairSlots][VPS];  // cos, sin, 1/d_c, alpha
+    __shared__ float4 s_pb[kPairSlots][VPS];  // gamma, g, column offset, window row of the lower slab's centre
+    __shared__ float s_zcr[kPairSlots][VPS];  // z_c / d_c (lower slab)
+    __shared__ int s_C[kPairSlots][VPS], s_skip[kPairSlots][VPS];
+
+    const int tiles = a.tps * a.tps;
+    const int q = blockIdx.x / tiles;
+    const int tt = blockIdx.x - q * tiles;
+    const int qy = q / a.m, qx = q - qy * a.m;
+    int ix0, ix1, iy0, iy1;
+    square_range(qx, a.m, a.N, ix0, ix1);
+    square_range(qy, a.m, a.N, iy0, iy1);
+    const int x0 = ix0 + (tt % a.tps) * kTile;
+    const int y0 = iy0 + (tt / a.tps) * kTile;
+    if (x0 > ix1 || y0 > iy1) return;  // ragged square: empty tile (uniform per CTA)
+    const int xe = min(x0 + kTile - 1, ix1), ye = min(y0 + kTile - 1, iy1);
+    const int p0 = a.pbase + blockIdx.y * kZP;  // first slice pair
+
+    const float half_n = 0.5f * (float)(a.N - 1);
+    const float xc = 0.5f * ((float)ix0 + (float)ix1) - half_n;
+    const float yc = 0.5f * ((float)iy0 + (float)iy1) - half_n;
+    // centre of the lower slab (the upper one is centred at -zc)
+    const float zc = (float)p0 + 0.5f * (float)(kZP - 1) - half_n;
+    const float vcd = 0.5f * (float)(a.Nv - 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nch = (a.nviews + VPS - 1) / VPS;
+    // window of view w of slot sl, lower (h = 0) or upper (h = 1) slab
+    auto win = [&](int sl, int w, int h) { return (uint32_t)((sl * VPS + w) * 2 + h) * (uint32_t)a.tile_stride; };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPairSlots; ++i) {
+            tma::mbar_init(&full[i], 1);
+            tma::mbar_init(&empty[i], kPairConsumers);
+        }
+        tma::fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kPairConsumers) {
+        // ---- producer: lanes 16 w .. 16 w + 15 set up view w of the chunk,
+        // 0-7 of them at the corners of the lower slab, 8-15 of the upper
+        const int32_t w0q = a.w0[q];
+        const int w = lane >> 4, cc = lane & 7;
+        const float zcl = (lane & 8) ? -zc : zc;
+        const float cx = (float)((cc & 1) ? xe : x0) - half_n - xc;
+        const float cy = (float)((cc & 2) ? ye : y0) - half_n - yc;
+        const float cz = (cc & 4) ? 0.5f * (float)(kZP - 1) : -0.5f * (float)(kZP - 1);
+        int c = 0;
+        for (; c < nch; ++c) {
+            const int sl = c % kPairSlots;
+            // round r of a slot may start once its round r - 1 was consumed
+            // (lane 0 waits; the warp follows its answer)
+            bool ok = true;
+            if (c >= kPairSlots && lane == 0)
+                ok = tma::mbar_wait_spin(&empty[sl], (uint32_t)(((c / kPairSlots) & 1) ^ 1), a.wait_ns);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                if (lane == 0) atomicOr(a.status, 2);
+                break;
+            }
+            const int nj = min(VPS, a.nviews - c * VPS);
+            const int j = c * VPS + min(w, nj - 1);  // lanes past the chunk repeat its last view
+            const int k = j * a.vstep;
+            const size_t o = (size_t)q * a.P + k;
+            const GeomEntry ge = a.geo[o];
+            const int cbase = DIRECT ? a.crop[o] : 0;
+            const float toff = DIRECT ? ge.frac - (float)w0q : -(float)w0q;
+            const float dd = fmaf(ge.cb, cx, ge.sb * cy);
+            const float invU = __fdividef(ge.g_hi, fmaf(ge.r, dd, 1.0f));
+            const float t = fmaf(invU, fmaf(ge.alpha, cx, ge.gamma * cy), toff);
+            const float zcr = zcl * ge.r;
+            // z_c g as hi + lo (exact product error by FMA)
+            const float ph = zcl * ge.g_hi;
+            const float pl = fmaf(zcl, ge.g_lo, fmaf(zcl, ge.g_hi, -ph));
+            const float v = (ph + vcd) + (pl + invU * (cz - zcr * dd));
+            float tmin = t, tmax = t, vmin = v, vmax = v;
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) {  // within each half's 8 corners
+                vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+            }
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {  // columns: both halves
+                tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
+                tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+            }
+            const float vmin2 = __shfl_down_sync(0xffffffffu, vmin, 8);
+            const float vmax2 = __shfl_down_sync(0xffffffffu, vmax, 8);
+            // lane 16 w: columns read floor(t) .. floor(t) + 1 over the tile,
+            // one sample of slack each side for FP32 rounding
+            const int clo = cbase + (int)floorf(tmin) - 1;
+            const int chi = cbase + (int)floorf(tmax) + 2;
+            const int xs = clo & ~(kAl - 1);  // 16-byte aligned start of the copy
+            const int vlo = (int)floorf(vmin) - 1, vhi = (int)floorf(vmax) + 2;
+            const int vlo2 = (int)floorf(vmin2) - 1, vhi2 = (int)floorf(vmax2) + 2;
+            const bool lead = (lane & 15) == 0 && w < nj;
+            if (lead) {
+                const int skip = (chi - xs > WD - 1) || (vhi - vlo > a.RW - 1) || (vhi2 - vlo2 > a.RW - 1) ||
+                                 a.fault == kTestFaultSmallWindow;
+                if (skip) atomicOr(a.status, 1);
+                s_pa[sl][w] = make_float4(ge.cb, ge.sb, ge.r, ge.alpha);
+                s_pb[sl][w] = make_float4(ge.gamma, ge.g_hi, toff - (float)(xs - cbase), (ph - ((float)vlo - vcd)) + pl);
+                s_zcr[sl][w] = zcr;
+                s_C[sl][w] = (a.Nv - 1) - vlo - vlo2;
+                s_skip[sl][w] = skip;
+            }
+            // the copies: lane 0 for every view of the chunk
+            const int xs0 = __shfl_sync(0xffffffffu, xs, 0), xs1 = __shfl_sync(0xffffffffu, xs, 16);
+            const int vl0 = __shfl_sync(0xffffffffu, vlo, 0), vl1 = __shfl_sync(0xffffffffu, vlo, 16);
+            const int vu0 = __shfl_sync(0xffffffffu, vlo2, 0), vu1 = __shfl_sync(0xffffffffu, vlo2, 16);
+            const int tz = DIRECT ? k : q * a.Pd + j;
+            const int tz0 = __shfl_sync(0xffffffffu, tz, 0), tz1 = __shfl_sync(0xffffffffu, tz, 16);
+            __syncwarp();  // the parameters are written before lane 0 publishes them
+            if (lane == 0) {
+                tma::fence_proxy_async();
+                tma::mbar_arrive_expect_tx(&full[sl], (uint32_t)(nj * 2 * a.RW * WD * ES));
+                for (int v2 = 0; v2 < nj; ++v2) {
+                    // test hook: the slot's bytes never all arrive, its wait runs out
+                    if (a.fault == kTestFaultSkipCopy && c == 1 && v2 == 0 && blockIdx.x == 0 && blockIdx.y == 0)
+                        continue;
+                    const int x = v2 == 0 ? xs0 : xs1, z = v2 == 0 ? tz0 : tz1;
+                    tma::load_3d(sm + win(sl, v2, 0), &tmap, &full[sl], x, v2 == 0 ? vl0 : vl1, z);
+                    tma::load_3d(sm + win(sl, v2, 1), &tmap, &full[sl], x, v2 == 0 ? vu0 : vu1, z);
+                }
+            }
+            __syncwarp();
+        }
+        // copies still in flight must land before the CTA may exit
+        if (lane == 0)
+            for (int m = max(0, c - kPairSlots); m < c; ++m)
+                tma::mbar_wait_bounded(&full[m % kPairSlots], (uint32_t)((m / kPairSlots) & 1), a.wait_ns);
+        return;
+    }
+
+    // ---- consumers
+    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool active = x <= xe && y <= ye;
+    const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
+    float lo[kZP], up[kZP];  // lower slab, upper (mirrored) slab
+#pragma unroll
+    for (int i = 0; i < kZP; ++i) lo[i] = up[i] = 0.f;
+
+    for (int c = 0; c < nch; ++c) {
+        const int sl = c % kPairSlots;
+        const bool ok = tma::mbar_wait_bounded(&full[sl], (uint32_t)((c / kPairSlots) & 1), a.wait_ns);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicOr(a.status, 2);
+            return;  // the producer waits for the copies in flight
+        }
+        const int nj = min(VPS, a.nviews - c * VPS);
+        for (int w = 0; w < nj; ++w) {
+            if (s_skip[sl][w]) continue;  // uniform per CTA
+            const float4 pa = s_pa[sl][w];
+            const float4 pb = s_pb[sl][w];
+            const float dd = fmaf(pa.x, dx, pa.y * dy);
+            const float invU = __fdividef(pb.y, fmaf(pa.z, dd, 1.0f));
+            const uint32_t dV = __float2uint_rn(invU * kFix);
+            // warp-uniform choice (threads outside a ragged tile do not constrain it)
+            const bool stepA = __all_sync(0xffffffffu, !active || dV <= (1u << 23));
+            if (!active) continue;
+            const float t = fmaf(invU, fmaf(pa.w, dx, pb.x * dy), pb.z);
+            const float tf = floorf(t);
+            const float wgt = invU * invU;
+            const float a1 = wgt * (t - tf);
+            const float a0 = wgt - a1;
+            // window row of slice p0 (lower slab), in 9.23 fixed point
+            const float vb0 = fmaf(invU, -0.5f * (float)(kZP - 1) - s_zcr[sl][w] * dd, pb.w);
+            uint32_t V = __float2uint_rn(vb0 * kFix);
+            // byte addresses: row r of the lower window at r ROWB + bL; the
+            // upper window's row C - 1 - r at KLU - (r ROWB + bL)
+            const uint32_t bL = sbase + (uint32_t)ES * (win(sl, w, 0) + (uint32_t)(int)tf);
+            const uint32_t bU = sbase + (uint32_t)ES * (win(sl, w, 1) + (uint32_t)(int)tf);
+            const uint32_t KLU = (uint32_t)(s_C[sl][w] - 1) * ROWB + bU + bL;
+            if (stepA) {
+                // 1/U <= 1: the row advances by 0 or 1 per slice
+                uint32_t r = V >> 23;
+                uint32_t aL = r * ROWB + bL, aU = KLU - aL;
+                float f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
+                float lA = fmaf(a1, Lds<TS, ES>::f(aL), a0 * Lds<TS, 0>::f(aL));
+                float lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
+                float uA = fmaf(a1, Lds<TS, ROWB + ES>::f(aU), a0 * Lds<TS, ROWB>::f(aU));
+                float uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
+                lo[0] = fmaf(f, lB - lA, lo[0] + lA);
+                up[0] = fmaf(f, uB - uA, up[0] + uA);
+#pragma unroll
+                for (int i = 1; i < kZP; ++i) {
+                    V += dV;
+                    const uint32_t rn = V >> 23;
+                    const bool adv = rn != r;
+                    r = rn;
+                    aL = r * ROWB + bL;
+                    aU = KLU - aL;
+                    f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
+                    lA = adv ? lB : lA;
+                    uA = adv ? uB : uA;
+                    lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
+                    uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
+                    lo[i] = fmaf(f, lB - lA, lo[i] + lA);
+                    up[i] = fmaf(f, uB - uA, up[i] + uA);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kZP; ++i) {
+                    const uint32_t r = V >> 23;
+                    const uint32_t aL = r * ROWB + bL, aU = KLU - aL;
+                    const float f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
+                    const float lA = fmaf(a1, Lds<TS, ES>::f(aL), a0 * Lds<TS, 0>::f(aL));
+                    const float lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
+                    const float uA = fmaf(a1, Lds<TS, ROWB + ES>::f(aU), a0 * Lds<TS, ROWB>::f(aU));
+                    const float uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
+                    lo[i] = fmaf(f, lB - lA, lo[i] + lA);
+                    up[i] = fmaf(f, uB - uA, up[i] + uA);
+                    V += dV;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) tma::mbar_arrive(&empty[sl]);  // this warp is done with the slot
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < kZP; ++i) {
+            const int pz = p0 + i;
+            if (pz < a.pend) {
+                const int zu = a.N - 1 - pz;
+                a.vol[((size_t)pz * a.N + y) * a.N + x] = lo[i] * a.scale;
+                if (zu != pz) a.vol[((size_t)zu * a.N + y) * a.N + x] = up[i] * a.scale;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent form for a batch of plans (float32 windows): one launch, as
 // many CTAs as fit the GPU, each taking work items (plan, tile, z-slab) from
 // an atomic counter until the list is exhausted; per item the arithmetic of
@@ -835,13 +1125,149 @@ cudaError_t try_launch_tma(const PlanImpl &p, const SquareSet &ss, bool direct, 
     return cudaErrorInvalidValue;
 }
 
+// dynamic shared memory of the pair kernel: kPairSlots slots of VPS views,
+// two windows per view, plus the 128-byte alignment slack
+inline size_t pair_smem(int es, int vps, int tile_stride) {
+    return (size_t)es * kPairSlots * vps * 2 * tile_stride + 128;
+}
+
+template <typename TS, bool DIRECT, int WD, int VPS>
+cudaError_t launch_pair_t(const CUtensorMap &map, const BpPairParams &prm, int nsq, cudaStream_t st) {
+    const size_t smem = pair_smem((int)sizeof(TS), VPS, prm.tile_stride);
+    cudaError_t e = ensure_smem<bp_pair_kernel<TS, DIRECT, WD, VPS>>(smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(nsq * prm.tps * prm.tps), (unsigned)((prm.pend - prm.pbase + kZP - 1) / kZP));
+    bp_pair_kernel<TS, DIRECT, WD, VPS><<<grid, kPairThreads, smem, st>>>(map, prm);
+    return cudaGetLastError();
+}
+
+// views per slot: 2 (three CTAs per SM hold their ring at the usual window
+// sizes), or 1 for larger windows (the staging depth only; the arithmetic and
+// the result are the same)
+template <typename TS, bool DIRECT, int WD>
+cudaError_t launch_pair_v(int vps, const CUtensorMap &map, const BpPairParams &prm, int nsq, cudaStream_t st) {
+    return vps == 2 ? launch_pair_t<TS, DIRECT, WD, 2>(map, prm, nsq, st)
+                    : launch_pair_t<TS, DIRECT, WD, 1>(map, prm, nsq, st);
+}
+
+template <typename TS, bool DIRECT>
+cudaError_t launch_pair_w(int WD, int vps, const CUtensorMap &map, const BpPairParams &prm, int nsq,
+                          cudaStream_t st) {
+    switch (WD) {
+        case 32: return launch_pair_v<TS, DIRECT, 32>(vps, map, prm, nsq, st);
+        case 48: return launch_pair_v<TS, DIRECT, 48>(vps, map, prm, nsq, st);
+        case 64: return launch_pair_v<TS, DIRECT, 64>(vps, map, prm, nsq, st);
+        case 96: return launch_pair_v<TS, DIRECT, 96>(vps, map, prm, nsq, st);
+        case 128: return launch_pair_v<TS, DIRECT, 128>(vps, map, prm, nsq, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// opt-in shared memory per block of the current device, less room for the
+// kernels' static shared memory; *per_sm: the SM's shared memory less what
+// the runtime reserves per block, shared by the CTAs of an SM
+size_t smem_budget(size_t *per_sm = nullptr) {
+    int dev = 0, optin = 0, sm = 0, reserved = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return 0;
+    if (per_sm) *per_sm = (size_t)sm;
+    return optin > 2048 ? (size_t)optin - 2048 : 0;
+}
+
+// The mirrored-pair kernel serves launches over the whole detector and the
+// slice pairs p0 .. p1 - 1 (slices p and N - 1 - p), with the TMA
+// conditions of make_tma_launch and windows of kZP slices.
+cudaError_t try_launch_pair(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
+                            cudaStream_t st, int p0, int p1, bool &launched) {
+    launched = false;
+    const int es = (direct && p.qtype != FDKOD_F32) ? 2 : 4;
+    const int WD = es == 4 ? ss.WdT : ss.WdT16;
+    if (WD == 0 || ss.Rw2 > 256 || ((uintptr_t)src & 15) != 0) return cudaSuccess;
+    if (direct && ((size_t)p.g.Nu * es) % 16 != 0) return cudaSuccess;
+    uint64_t dims[3], strides[2];
+    if (direct) {
+        dims[0] = (uint64_t)p.g.Nu;
+        dims[1] = (uint64_t)p.g.Nv;
+        dims[2] = (uint64_t)p.g.P;
+        strides[0] = (uint64_t)p.g.Nu * es;
+    } else {
+        dims[0] = (uint64_t)p.Tstride;
+        dims[1] = (uint64_t)p.g.Nv;
+        dims[2] = (uint64_t)ss.nsq * p.Pd;
+        strides[0] = (uint64_t)p.Tstride * sizeof(float);
+    }
+    strides[1] = strides[0] * dims[1];
+    const uint32_t box[3] = {(uint32_t)WD, (uint32_t)ss.Rw2, 1u};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (p.qtype == FDKOD_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUtensorMap map;
+    if (encode_map_3d(&map, dt, src, dims, strides, box) != cudaSuccess) return cudaSuccess;
+    BpPairParams a{};
+    a.vol = vol;
+    a.geo = ss.geo;
+    a.crop = ss.crop;
+    a.w0 = ss.w0;
+    a.status = p.status;
+    a.N = p.g.N;
+    a.P = p.g.P;
+    a.Nv = p.g.Nv;
+    a.m = ss.m;
+    a.tps = ss.tiles_per_side;
+    a.Pd = p.Pd;
+    a.RW = ss.Rw2;
+    a.tile_stride = (ss.Rw2 * WD + (128 / es - 1)) & ~(128 / es - 1);
+    size_t per_sm = 0;
+    const size_t budget = smem_budget(&per_sm);
+    // 2 views per slot where three CTAs fit an SM (each with its static
+    // shared memory and the runtime's reserve, 2 KiB together at most), else
+    // 1 if one CTA fits
+    const int vps = 3 * (pair_smem(es, 2, a.tile_stride) + 2048) <= per_sm ? 2
+                    : (pair_smem(es, 1, a.tile_stride) <= budget ? 1 : 0);
+    if (vps == 0) return cudaSuccess;  // windows too large: the 32-slice kernel
+    a.pbase = p0;
+    a.pend = p1;
+    a.wait_ns = p.wait_ns > 0 ? (unsigned long long)p.wait_ns : kWaitLimitNs;
+    a.fault = p.test_fault;
+    if (direct) {
+        a.nviews = p.g.P;
+        a.vstep = 1;
+        a.scale = (float)(M_PI / (double)p.g.P);
+    } else {
+        a.nviews = p.Pd;
+        a.vstep = p.D;
+        a.scale = (float)(M_PI / (double)p.Pd);
+    }
+    launched = true;
+    if (!direct) return launch_pair_w<float, false>(WD, vps, map, a, ss.nsq, st);
+    switch (p.qtype) {
+        case FDKOD_F32: return launch_pair_w<float, true>(WD, vps, map, a, ss.nsq, st);
+        case FDKOD_BF16: return launch_pair_w<__nv_bfloat16, true>(WD, vps, map, a, ss.nsq, st);
+        case FDKOD_F16: return launch_pair_w<__half, true>(WD, vps, map, a, ss.nsq, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+cudaError_t launch_backproject_pairs(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
+                                     float *vol, cudaStream_t st, int p0, int p1, bool &launched) {
+    return try_launch_pair(p, ss, direct, src, vol, st, p0, p1, launched);
+}
 
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src, float *vol,
                                cudaStream_t st, Band b) {
+    const bool whole = b.row0 == 0 && (b.nrows < 0 || b.nrows == p.g.Nv) && b.zoff == 0 && (b.nz < 0 || b.nz == p.g.N);
     if (b.nrows < 0) b.nrows = p.g.Nv;
     if (b.nz < 0) b.nz = p.g.N;
     bool launched = false;
+    if (whole) {
+        cudaError_t pe = try_launch_pair(p, ss, direct, src, vol, st, 0, (p.g.N + 1) / 2, launched);
+        if (launched || pe != cudaSuccess) return pe;
+    }
     cudaError_t te = try_launch_tma(p, ss, direct, src, vol, st, b, launched);
     if (launched || te != cudaSuccess) return te;
     BpParams a{};

@@ -39,12 +39,14 @@ struct SquareSet {
     // (4-element alignment slack, rounded up to a kernel instantiation, 0
     // when no instantiation is wide enough)
     int Wd = 0, Rw = 0, WdT = 0, WdT16 = 0;  // WdT16: the same for 16-bit windows
+    int Rw2 = 0;  // rows of a window of kZP slices (the mirrored-pair kernel)
     int need = 0, need16 = 0;  // the narrowest TMA windows that hold every tile's footprint
     int tiles_per_side = 1;  // 16-voxel tiles per square side
 };
 
 constexpr int kTile = 16;      // tile side in x and y (threads per CTA = 256)
 constexpr int kZT = 32;        // z voxels per thread
+constexpr int kZP = 16;        // slices per half of the mirrored-pair kernel (2 kZP voxels per thread)
 constexpr int kViewsPerChunk = 8;  // generic backprojection kernel
 constexpr int kViewsPerStage = 4;  // TMA backprojection kernel (two stages)
 constexpr int kMaxTapD = 128;      // largest decimation factor with a tap table
@@ -80,6 +82,7 @@ struct PlanImpl {
     int L = 0, log2L = 0;
     float *H = nullptr;        // ramp spectrum / L, real and even
     float2 *tw = nullptr;      // e^{-2 pi i m / L}, m < L
+    float2 *tw2 = nullptr;     // L = 1024: e^{-2 pi i a b / 1024} at a * 32 + b, a, b < 32
     // angular low-pass of the decomposition (Sec. 2.1): symmetric taps
     // h[|i|], |i| < H D with H = tap_blocks (triangle by default, H = 1), and
     // per block offset r the weights of the 2H running sums,
@@ -159,6 +162,11 @@ cudaError_t launch_net_decompose(const PlanImpl &p, const void *Q, float *out, c
 cudaError_t upload_net(PlanImpl &p);
 cudaError_t launch_backproject(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
                                float *vol, cudaStream_t st, Band b = Band{});
+// The mirrored-pair backprojection of slice pairs p0 .. p1 - 1 (slices p and
+// N - 1 - p, whole detector; vol is the whole volume); launched = false when
+// the staged pair kernel does not apply (then nothing is launched).
+cudaError_t launch_backproject_pairs(const PlanImpl &p, const SquareSet &ss, bool direct, const void *src,
+                                     float *vol, cudaStream_t st, int p0, int p1, bool &launched);
 
 // A batch of plans backprojected by one persistent launch (backproject.cu):
 // per plan its FDK-OD source (Q when D = 1, else the decomposed data) and

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "fdkod_internal.cuh"
+#include "tma.cuh"
 
 namespace fdkod {
 namespace {
@@ -284,11 +285,192 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
     fft<kToQ>(buf, tw, lgL, lt, nt, sink);
 }
 
+// ---------------------------------------------------------------------------
+// Warp form for L = 1024 (detector rows of 257 .. 512 columns): one warp per
+// row pair, the transform of length 1024 = 32 x 32 done as a 32-point DFT
+// in every lane's registers, one twiddle multiply, a transpose through a
+// padded 32 x 33 tile of shared memory and a second 32-point DFT.  Input
+// sample n = 32 n1 + n2 sits in lane n2, register n1 (coalesced loads; n1 <
+// 16 since the upper half is padding); after the forward transform lane k1
+// holds X[k1 + 32 k2] in register k2, multiplies by the ramp spectrum,
+// conjugates, and the same two steps run again; output sample n = n1 +
+// 32 n2 ends in lane n1, register n2 (coalesced stores).  No block barrier:
+// each warp only synchronises with itself around its transposes.
+
+constexpr int kFilterWarps = 4;  // row pairs per CTA
+
+// W32^k = e^{-2 pi i k / 32}, k = 0 .. 15: cos(k pi / 16) and sin(k pi / 16)
+__device__ __forceinline__ constexpr float cos16(int k) {
+    return k == 0 ? 1.0f : k == 1 ? 0.98078528040323044913f : k == 2 ? 0.92387953251128675613f
+         : k == 3 ? 0.83146961230254523708f : k == 4 ? 0.70710678118654752440f : k == 5 ? 0.55557023301960222474f
+         : k == 6 ? 0.38268343236508977173f : k == 7 ? 0.19509032201612826785f : k == 8 ? 0.0f : -cos16(16 - k);
+}
+__device__ __forceinline__ constexpr float sin16(int k) { return k <= 8 ? cos16(8 - k) : cos16(k - 8); }
+
+// 32-point forward DFT in registers, in place, by decimation in frequency:
+// u[n] = v[n] + v[n + 16] and w[n] = (v[n] - v[n + 16]) W32^n for n < 16,
+// then X[2k] = DFT16(u)[k] and X[2k + 1] = DFT16(w)[k].  Input in natural
+// order; X[k] is left at v[pos32(k)].  HALF: v[16 ..] are zero on input.
+__device__ __forceinline__ constexpr int pos32(int k) {
+    return (k & 1) ? 16 + out_pos<16>(k >> 1) : out_pos<16>(k >> 1);
+}
+
+template <bool HALF = false>
+__device__ __forceinline__ void dft32(float2 *v) {
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        const float2 a = v[n], b = v[n + 16];
+        float2 d = HALF ? a : csub(a, b);
+        if (!HALF) v[n] = cadd(a, b);
+        if (n == 8) d = cmi(d);
+        else if (n != 0) d = cmul(d, make_float2(cos16(n), -sin16(n)));
+        v[n + 16] = d;
+    }
+    dft<16>(v);
+    dft<16>(v + 16);
+}
+
+constexpr int kTile32 = 32 * 33;                  // padded 32 x 32 transpose tile (float2)
+constexpr int kStage = 1024;                      // floats of a staged row pair (2 rows of <= 512)
+constexpr uint64_t kFilterWaitNs = 2000000000ull;  // bounded wait on a staged row pair
+// dynamic shared memory: per warp a staging buffer and a transpose tile,
+// then the twiddles W1024^(a b) and the ramp spectrum
+constexpr size_t kFilterSmem =
+    128 + (size_t)kFilterWarps * (kStage * sizeof(float) + kTile32 * sizeof(float2)) + 1024 * (sizeof(float2) + sizeof(float));
+
+template <typename TQ>
+__global__ void __launch_bounds__(32 * kFilterWarps, 3)
+filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
+                   const float2 *__restrict__ tw2, int Nu, int Nv, int row0, int rows_per_view, int nrows, float R,
+                   int *status) {
+    extern __shared__ __align__(128) unsigned char fsm_raw[];
+    unsigned char *base = fsm_raw + ((128u - (tma::smem_u32(fsm_raw) & 127u)) & 127u);
+    float(*stg)[kStage] = reinterpret_cast<float(*)[kStage]>(base);
+    float2(*tile)[kTile32] = reinterpret_cast<float2(*)[kTile32]>(base + kFilterWarps * kStage * sizeof(float));
+    float2 *s_tw = reinterpret_cast<float2 *>(base + kFilterWarps * (kStage * sizeof(float) + kTile32 * sizeof(float2)));
+    float *s_h = reinterpret_cast<float *>(s_tw + 1024);
+    __shared__ __align__(8) uint64_t bar[kFilterWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        s_tw[i] = tw2[i];
+        s_h[i] = H[i];
+    }
+    if (lane == 0) {
+        tma::mbar_init(&bar[warp], 1);
+        tma::fence_mbar_init();
+    }
+    __syncthreads();
+    const int npairs = (nrows + 1) / 2;
+    const int stride = gridDim.x * kFilterWarps;
+    float *in = stg[warp];
+    float2 *t = tile[warp];
+    // rows 2 pr and 2 pr + 1 are adjacent in memory: one copy
+    auto stage = [&](int pr) {
+        const int rows = min(2, nrows - 2 * pr);
+        const uint32_t bytes = (uint32_t)(rows * Nu) * 4u;
+        tma::fence_proxy_async();
+        tma::mbar_arrive_expect_tx(&bar[warp], bytes);
+        tma::bulk_load(in, proj + (size_t)(2 * pr) * Nu, bytes, &bar[warp]);
+    };
+    int pair = blockIdx.x * kFilterWarps + warp;
+    if (pair < npairs && lane == 0) stage(pair);
+    const float R2 = R * R;
+    for (int it = 0; pair < npairs; ++it, pair += stride) {
+        if (!tma::mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), kFilterWaitNs)) {
+            // the copy never completed: report, give it a last chance to land, leave
+            if (lane == 0) atomicOr(status, 2);
+            tma::mbar_wait_bounded(&bar[warp], (uint32_t)(it & 1), kFilterWaitNs);
+            return;
+        }
+        const int rowA = 2 * pair, rowB = rowA + 1;
+        const bool hasB = rowB < nrows;
+        const float bA = (float)(row0 + rowA % rows_per_view) - 0.5f * (float)(Nv - 1);
+        const float bB = (float)(row0 + rowB % rows_per_view) - 0.5f * (float)(Nv - 1);
+        float2 v[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const int n = 32 * n1 + lane;
+            float2 x = make_float2(0.f, 0.f);
+            if (n < Nu) {
+                const float u = (float)n - 0.5f * (float)(Nu - 1);
+                x.x = in[n] * (R * rsqrtf(R2 + u * u + bA * bA));
+                if (hasB) x.y = in[Nu + n] * (R * rsqrtf(R2 + u * u + bB * bB));
+            }
+            v[n1] = x;
+        }
+#pragma unroll
+        for (int n1 = 16; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
+        // the input is in registers: the staging buffer takes the next pair
+        __syncwarp();
+        if (pair + stride < npairs && lane == 0) stage(pair + stride);
+        // two passes of the same code (one copy of it keeps the loop body in
+        // the instruction cache): lane a transforms over its 32 values,
+        // twiddles by W1024^(a b), and the transpose hands lane b the values
+        // of every a, which it transforms again.  Pass 0 is the forward
+        // transform (a = n2, b = k1), followed by the product with the ramp
+        // spectrum (over L) and the conjugation; pass 1 is the inverse as the
+        // conjugate of a forward transform (a = k1, b = n1).
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            dft32(v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) t[k * 33 + lane] = cmul(v[pos32(k)], s_tw[k * 32 + lane]);
+            __syncwarp();
+#pragma unroll
+            for (int n = 0; n < 32; ++n) v[n] = t[lane * 33 + n];
+            __syncwarp();
+            dft32(v);
+            if (pass == 0) {
+                // X[lane + 32 k2] sits at v[pos32(k2)]: spectrum product,
+                // conjugation, natural order for the next pass
+                float2 g[32];
+#pragma unroll
+                for (int k2 = 0; k2 < 32; ++k2) {
+                    const float h = s_h[lane + 32 * k2];
+                    const float2 x = v[pos32(k2)];
+                    g[k2] = make_float2(x.x * h, -x.y * h);
+                }
+#pragma unroll
+                for (int k2 = 0; k2 < 32; ++k2) v[k2] = g[k2];
+            }
+        }
+        // sample n = lane + 32 n2 of the conjugated result: row A real, row B imaginary
+        TQ *qa = Q + (size_t)rowA * Nu, *qb = qa + Nu;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) {
+            const int n = lane + 32 * n2;
+            if (n < Nu) {
+                const float2 y = v[pos32(n2)];
+                qa[n] = to_q<TQ>(y.x);
+                if (hasB) qb[n] = to_q<TQ>(-y.y);
+            }
+        }
+    }
+}
+
 template <typename TQ>
 cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st, int row0, int rows_per_view,
                      int views) {
     const long long nrows = (long long)views * rows_per_view;
     const long long pairs = (nrows + 1) / 2;
+    // the warp form stages rows with bulk copies: 16-byte aligned rows
+    if (p.L == 1024 && p.tw2 && (p.g.Nu % 4) == 0 && ((uintptr_t)proj & 15) == 0 && nrows < (1LL << 30)) {
+        // as many CTAs as the GPU holds at once (each warp loops over pairs)
+        const size_t smem = kFilterSmem;
+        cudaError_t e = ensure_smem<filter_1024_kernel<TQ>>(smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_1024_kernel<TQ>, 32 * kFilterWarps,
+                                                               smem)) != cudaSuccess)
+            return e;
+        const long long need = (pairs + kFilterWarps - 1) / kFilterWarps;
+        const long long blocks = std::max(1LL, std::min(need, (long long)std::max(1, per_sm) * sms));
+        filter_1024_kernel<TQ><<<(unsigned)blocks, 32 * kFilterWarps, smem, st>>>(
+            proj, Q, p.H, p.tw2, p.g.Nu, p.g.Nv, row0, rows_per_view, (int)nrows, (float)p.g.R, p.status);
+        return cudaGetLastError();
+    }
     const int G = std::max(1, 2048 / p.L);  // 128 threads per CTA up to L = 2048
     const long long blocks = (pairs + G - 1) / G;
     const size_t smem = sizeof(float2) * (size_t)G * (p.L + p.L / 16);

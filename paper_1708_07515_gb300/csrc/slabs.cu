@@ -249,17 +249,40 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
                                       fdkod::Band{}, nv));
     }
     if (p.D > 1) SLAB_TRY(fdkod::launch_decompose(p, hp.Q, p.Sp, comp));
-    // backprojection in z-slabs of whole 32-slice tiles; read-back overlapped
+    const bool direct = p.D == 1;
+    const void *src = direct ? hp.Q : (const void *)p.Sp;
+    // backprojection in groups of slice pairs (slices p and N - 1 - p, the
+    // same tiles as one whole-volume launch); each group's two z-ranges are
+    // read back while the next group is computed
+    const int npair = (N + 1) / 2;
+    int ps = (npair + kPipeSlabs - 1) / kPipeSlabs;
+    ps = (ps + fdkod::kZP - 1) / fdkod::kZP * fdkod::kZP;
+    int ns = 0;
+    bool paired = true;
+    for (int pa = 0; pa < npair && paired; pa += ps, ++ns) {
+        const int pb = std::min(pa + ps, npair);
+        SLAB_TRY(fdkod::launch_backproject_pairs(p, p.od, direct, src, hp.vol, comp, pa, pb, paired));
+        if (!paired) break;  // not staged: z-slabs below (before anything was launched)
+        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], comp));
+        SLAB_TRY(cudaStreamWaitEvent(hp.down, hp.ev_slab[ns], 0));
+        const size_t plane = (size_t)N * N;
+        SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)pa * plane, hp.vol + (size_t)pa * plane,
+                                 sizeof(float) * (size_t)(pb - pa) * plane, cudaMemcpyDeviceToHost, hp.down));
+        const int u0 = std::max(N - pb, pb), u1 = N - pa;  // upper slices, the middle one (odd N) once
+        if (u1 > u0)
+            SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)u0 * plane, hp.vol + (size_t)u0 * plane,
+                                     sizeof(float) * (size_t)(u1 - u0) * plane, cudaMemcpyDeviceToHost, hp.down));
+    }
+    // z-slabs of whole 32-slice tiles where the staged pair kernel does not apply
     int zs = (N + kPipeSlabs - 1) / kPipeSlabs;
     zs = (zs + fdkod::kZT - 1) / fdkod::kZT * fdkod::kZT;
-    int ns = 0;
-    for (int z0 = 0; z0 < N; z0 += zs, ++ns) {
+    if (!paired) ns = 0;
+    for (int z0 = 0; z0 < N && !paired; z0 += zs, ++ns) {
         fdkod::Band b;
         b.zoff = z0;
         b.nz = std::min(zs, N - z0);
         float *dst = hp.vol + (size_t)z0 * N * N;
-        if (p.D == 1) SLAB_TRY(fdkod::launch_backproject(p, p.od, true, hp.Q, dst, comp, b));
-        else SLAB_TRY(fdkod::launch_backproject(p, p.od, false, p.Sp, dst, comp, b));
+        SLAB_TRY(fdkod::launch_backproject(p, p.od, direct, src, dst, comp, b));
         SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], comp));
         SLAB_TRY(cudaStreamWaitEvent(hp.down, hp.ev_slab[ns], 0));
         SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)z0 * N * N, dst, sizeof(float) * (size_t)b.nz * N * N,

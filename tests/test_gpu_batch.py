@@ -53,9 +53,12 @@ def test_graph_batch_matches_eager_and_oracle(fd, oracle_mod):
 
 @pytest.mark.parametrize("persistent", [True, False])
 def test_persistent_batch_equals_per_plan_launches(fd, oracle_mod, persistent):
-    """The persistent kernel (one launch, work list over volumes, tiles and
-    z-slabs; plans with D = 1 read Q, the others their workspace) gives each
-    volume bit for bit what its own backprojection launch gives."""
+    """The batch graph's per-volume branches give each volume bit for bit
+    what its own backprojection launch gives.  The persistent kernel (one
+    launch, work list over volumes, tiles and z-slabs of 32 slices; plans
+    with D = 1 read Q, the others their workspace) evaluates the same sums
+    with the row coordinate in float32 where the per-volume launch (slice
+    pairs) uses fixed point: equal to float32 rounding."""
     from paper_1708_07515_gb300.batch import BatchReconstructor, Instance
     insts = [Instance(4.0 * 48, 48, 48, 48, 64, 2, 4), Instance(4.0 * 40, 40, 44, 36, 60, 0, 1),
              Instance(4.0 * 64, 64, 64, 64, 90, 3, 3), Instance(4.0 * 33, 33, 36, 40, 48, 1, 2)]
@@ -71,7 +74,12 @@ def test_persistent_batch_equals_per_plan_launches(fd, oracle_mod, persistent):
         for inst, plan, Q, v in zip(insts, br.plans, br.Q, br.vol):
             ref = plan.backproject(Q)
             torch.cuda.synchronize()
-            assert torch.equal(v, ref), inst
+            if persistent:
+                d = (v.double() - ref.double())
+                assert float(d.norm() / ref.double().norm()) <= 1e-6, inst
+                assert float(d.abs().max() / ref.abs().max()) <= 2e-5, inst
+            else:
+                assert torch.equal(v, ref), inst
             assert plan.device_status() == 0
         # and against the oracle (parity bar)
         for inst, p, v in zip(insts, projs, br.vol):
