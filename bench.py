@@ -551,8 +551,9 @@ def main():
     # --- end to end through the library's host-buffer call (fdkod_reconstruct):
     # every step uploads the scan's projections from page-locked host memory
     # and reads the whole volume back into it, inside the call (uploads in
-    # view chunks overlap the filter, read-backs of z-slabs overlap the
-    # backprojection); the call is synchronous, so the host clock times it
+    # bands of detector rows overlap the filter and the decomposition,
+    # read-backs of groups of slices overlap the backprojection); the call is
+    # synchronous, so the host clock times it
     if args.no_e2e:
         ms_e2e, n_e2e = None, 0
     else:
@@ -649,8 +650,9 @@ def main():
                 "h2d_bytes_per_step": proj.nbytes, "d2h_bytes_per_step": w.N ** 3 * 4,
                 "ms_per_step": ms_e2e, "steps": n_e2e,
                 "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
-                "note": "host clock around whole calls; inside a call the upload (view chunks) overlaps the "
-                        "filter and the read-back (z-slabs) overlaps the backprojection"},
+                "note": "host clock around whole calls; inside a call the upload (bands of detector rows) "
+                        "overlaps the filter and the decomposition, the read-back (groups of slices) the "
+                        "backprojection"},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "kernel": "FDK-OD backprojection",
                          "achieved": ops_ach, "peak": ops_peak, "unit": "TFLOP/s",

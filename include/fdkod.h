@@ -93,7 +93,7 @@ typedef struct {
  * it with fdkod_destroy.  Errors: INVALID_ARG (null g/out, non-positive
  * sizes, R <= 0, unknown qtype), UNSUPPORTED (P % D != 0, s < 0,
  * s > 7, 2^s > N, R not beyond the volume, sizes above 2^15, Nu above
- * 2048), OOM, CUDA.
+ * 8192), OOM, CUDA.
  */
 int fdkod_plan(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, fdkod_plan_t **out);
 
@@ -302,11 +302,14 @@ int fdkod_noalloc_device_status(uintptr_t stream);
  * proj_host: host [P][Nv][Nu] float32; vol_host: host [N][N][N] float32,
  * fully overwritten.  Page-locked host memory lets the copies overlap the
  * compute; pageable memory works, with synchronous copies.  Within the call
- * the projections are uploaded in chunks of views and each chunk is
- * filtered as soon as it has landed; after the decomposition the volume is
- * backprojected in z-slabs and each slab is copied back while the next one
- * is computed (an upload and a read-back stream of the plan's own, ordered
- * after the work already queued on `stream`).
+ * the projections are uploaded in bands of detector rows and each band is
+ * filtered and decomposed as soon as it has landed (both stages are
+ * row-local); the volume is then backprojected in groups of slices and each
+ * group is copied back while the next one is computed (an upload and a
+ * read-back stream of the plan's own, ordered after the work already queued
+ * on `stream`).  The volume equals fdkod_filter + fdkod_backproject bit for
+ * bit when Nv is even (for odd Nv the filter pairs rows differently: equal
+ * to float32 round-off).
  * Device memory: the first call allocates, and the plan then keeps until
  * fdkod_destroy, buffers for the projections, the filtered projections and
  * the volume (reported in fdkod_plan_info.device_bytes); the plan must have

@@ -331,9 +331,10 @@ int fdkod_plan_ex(const fdkod_geometry *g, int s, int D, fdkod_dtype qtype, int 
         return FDKOD_ERR_INVALID_ARG;
     const int lim = 1 << 15;
     if (g->N > lim || g->Nu > lim || g->Nv > lim || g->P > lim) return FDKOD_ERR_UNSUPPORTED;
-    // the filter's shared-memory FFT holds two buffers of 2^ceil(log2(2 Nu))
-    // complex floats and uses one thread per 4 samples (at most 1024)
-    if (g->Nu > 2048) return FDKOD_ERR_UNSUPPORTED;
+    // the filter's shared-memory FFT of length L = 2^ceil(log2(2 Nu)) uses
+    // one thread per 16 samples (at most 1024: L <= 16384) and L (1 + 1/16)
+    // complex floats of shared memory (139 KiB at L = 16384)
+    if (g->Nu > 8192) return FDKOD_ERR_UNSUPPORTED;
     if (s < 0 || s > 7 || (1 << s) > g->N || g->P % D != 0 || D > fdkod::kMaxTapD) return FDKOD_ERR_UNSUPPORTED;
     // the source must lie outside the volume's circumscribed cylinder
     if (!(g->R > M_SQRT2 * 0.5 * (double)g->N + 1.0)) return FDKOD_ERR_UNSUPPORTED;

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "fdkod_internal.cuh"
 #include "tma.cuh"
@@ -37,11 +38,11 @@ template <typename TQ, int H>
 __global__ void __launch_bounds__(kTX *kTY)
 decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t *__restrict__ crop,
                  const GeomEntry *__restrict__ geo, const int32_t *__restrict__ Tq, const float4 *__restrict__ tapw,
-                 int Tstride, int P, int D, int Pd, int Nv, int Nu) {
+                 int Tstride, int P, int D, int Pd, int Nv, int Nu, int rowoff, int rowend) {
     const int t = blockIdx.x * kTX + threadIdx.x;
-    const int v = blockIdx.y * kTY + threadIdx.y;
+    const int v = rowoff + blockIdx.y * kTY + threadIdx.y;
     const int q = blockIdx.z;
-    if (t >= Tstride || v >= Nv) return;
+    if (t >= Tstride || v >= rowend) return;
     const size_t vstride = (size_t)Nv * Tstride;
     float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + t;
     if (t >= Tq[q]) {
@@ -96,22 +97,26 @@ decompose_kernel(const TQ *__restrict__ Q, float *__restrict__ Sp, const int32_t
 // its bytes have landed (mbarrier full[n]) and free again when all consumer
 // warps have arrived on empty[n].  No block-wide barrier inside the view loop.
 //
-// Consumers: LPR lanes share a pair of adjacent detector rows and each lane
-// owns C consecutive columns t0 .. t0 + C - 1 of both (rows_per_lane), so one
-// view costs the lane a few vector shared loads at compile-time offsets per
-// row (the column offset of the crop inside its aligned box selects one of
-// four code paths, uniform per view) and, per column, one lerp and the 2H
-// tap FMAs; the per-view bookkeeping is shared by the two rows.  Everything else
+// Consumers: the 32 lanes of a warp share its rows (rows_per_lane adjacent
+// detector rows) and lane l owns the columns l, l + 32, ... (C of them), so
+// per view and column a lane makes two scalar shared loads at the crop's
+// offset inside its aligned box plus compile-time offsets -- consecutive
+// lanes read consecutive elements, free of bank conflicts for every offset
+// -- one lerp and the 2H tap FMAs; the per-view bookkeeping is shared by the
+// lane's rows and columns.  (Lanes that owned C consecutive columns loaded
+// them as aligned vectors and picked the offset's code path per view: about
+// 20 instructions per shifted sample, issue-bound.)  Everything else
 // a view needs -- shift fraction, which tap weights apply and whether a
 // decimated view is complete -- is one 8-byte entry of a per-CTA table in
 // stream order, built once from crop[q][.] and frac[q][.], plus the weights
 // w[r] of its block offset r (one 16-byte entry per r).
 
 constexpr int kConsumerWarps = 8;
-// adjacent detector rows per lane (the per-view work is shared): two with
-// the triangle's two running sums, one with the four of 2D-tap filters
-// (registers; measured)
-__host__ __device__ constexpr int rows_per_lane(int H) { return H == 1 ? 2 : 1; }
+// adjacent detector rows per lane (the per-view bookkeeping -- table loads,
+// slot waits, decimated-view stores -- is shared by them): four with the
+// triangle's two running sums, two with the four of 2D-tap filters
+// (registers; measured: 2 -> 4 rows took 1.63 -> 1.48 ms at 512^3)
+__host__ __device__ constexpr int rows_per_lane(int H) { return H == 1 ? 4 : 2; }
 // ring shape per element type (measured): slots of kG views, kStages slots
 template <typename TQ>
 struct Ring {
@@ -119,7 +124,12 @@ struct Ring {
     static constexpr int kStages = 3;
 };
 constexpr int kDecThreads = 32 * (kConsumerWarps + 1);
-constexpr int kRingSlack = 128;  // bytes after the ring: vector loads of the last row may run past its end
+// bytes after the ring: a lane's columns run up to 32 C + 1 elements (plus
+// the crop's offset, < 16 bytes) past its row's start, beyond the last row's
+// Wc columns; rounded up to 128 bytes so the tables behind it (float4 and
+// float2 entries) stay aligned
+__host__ __device__ constexpr int kColSlack(int C) { return (4 * (32 * C + 1) + 16 + 127) & ~127; }
+static_assert(kColSlack(1) % 16 == 0 && kColSlack(8) % 16 == 0, "table alignment");
 constexpr uint64_t kDecWaitNs = 2000000000ull;
 
 // code word of a table entry: bits 0-2 the crop's offset inside its aligned
@@ -154,116 +164,94 @@ __device__ __forceinline__ void build_stream_table(float2 *s_fc, int *s_c, float
     for (int r = threadIdx.x; r < D; r += blockDim.x) s_taps[r] = tapw[r];
 }
 
-// NV vectors of 4 consecutive elements from 32-bit shared address a, widened to float
-template <typename TQ, int NV>
-struct VecLoad;
-template <int NV>
-struct VecLoad<float, NV> {
-    static __device__ __forceinline__ void f(uint32_t a, float *e) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                         : "=f"(e[4 * k]), "=f"(e[4 * k + 1]), "=f"(e[4 * k + 2]), "=f"(e[4 * k + 3])
-                         : "r"(a + 16u * k)
-                         : "memory");
+// One element at a compile-time byte offset from 32-bit shared address a,
+// widened to float.
+template <typename TQ, int OFF>
+struct Ld1;
+template <int OFF>
+struct Ld1<float, OFF> {
+    static __device__ __forceinline__ float f(uint32_t a) {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF) : "memory");
+        return v;
     }
 };
-template <int NV>
-struct VecLoad<__nv_bfloat16, NV> {
-    static __device__ __forceinline__ void f(uint32_t a, float *e) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            uint32_t w0, w1;
-            asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(a + 8u * k) : "memory");
-            // bfloat16 is the top half of a float32
-            e[4 * k] = __uint_as_float(w0 << 16);
-            e[4 * k + 1] = __uint_as_float(w0 & 0xffff0000u);
-            e[4 * k + 2] = __uint_as_float(w1 << 16);
-            e[4 * k + 3] = __uint_as_float(w1 & 0xffff0000u);
-        }
+template <int OFF>
+struct Ld1<__nv_bfloat16, OFF> {
+    static __device__ __forceinline__ float f(uint32_t a) {
+        uint32_t u;
+        asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(u) : "r"(a), "n"(OFF) : "memory");
+        return __uint_as_float(u << 16);  // bfloat16 is the top half of a float32
     }
 };
-template <int NV>
-struct VecLoad<__half, NV> {
-    static __device__ __forceinline__ void f(uint32_t a, float *e) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            uint32_t w0, w1;
-            asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(a + 8u * k) : "memory");
-            const float2 p0 = __half22float2(*reinterpret_cast<const __half2 *>(&w0));
-            const float2 p1 = __half22float2(*reinterpret_cast<const __half2 *>(&w1));
-            e[4 * k] = p0.x;
-            e[4 * k + 1] = p0.y;
-            e[4 * k + 2] = p1.x;
-            e[4 * k + 3] = p1.y;
-        }
+template <int OFF>
+struct Ld1<__half, OFF> {
+    static __device__ __forceinline__ float f(uint32_t a) {
+        unsigned short h;
+        asm volatile("ld.shared.u16 %0, [%1+%2];" : "=h"(h) : "r"(a), "n"(OFF) : "memory");
+        return __half2float(__ushort_as_half(h));
     }
 };
 
-// One view for one lane: in each of its RPL rows (row stride rs bytes),
-// columns t0 + i (i < C) sample the row at box column O + i (+ the shift
-// fraction f) and feed that row's 2H running sums with weights w.
-template <typename TQ, int C, int O, int H, int RPL>
-__device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, float4 w, float (*acc)[2 * H][C]) {
-    constexpr int NV = (O + C) / 4 + 1;  // vectors covering elements O .. O + C
-#pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-        float e[4 * NV];
-        VecLoad<TQ, NV>::f(a + rs * (uint32_t)r, e);
-#pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const float a0 = e[O + i], a1 = e[O + i + 1];
-            const float smp = fmaf(f, a1 - a0, a0);
-            acc[r][0][i] = fmaf(w.x, smp, acc[r][0][i]);
-            acc[r][1][i] = fmaf(w.y, smp, acc[r][1][i]);
-            if (H == 2) {
-                acc[r][2][i] = fmaf(w.z, smp, acc[r][2][i]);
-                acc[r][3][i] = fmaf(w.w, smp, acc[r][3][i]);
-            }
-        }
+// One view for one lane: in each of its RPL rows (row stride rs bytes), the
+// columns t = lane + 32 i (i < C, t < T) sample the row at box column
+// off + t (+ the shift fraction f) and feed that row's 2H running sums with
+// weights w.  a is the byte address of box column off + lane of the lane's
+// first row, so consecutive lanes read consecutive elements (no bank
+// conflicts) whatever the crop's offset off inside its aligned box.
+// Columns past T are computed too (no branch; their sums are never stored):
+// their loads stay inside the CTA's shared memory, within the next row, the
+// next slot or the ring's tail slack of kColSlack(C) bytes.
+template <typename TQ, int I, int C, int H>
+__device__ __forceinline__ void col_step(uint32_t ar, float f, float4 w, float (&acc)[2 * H][C]) {
+    constexpr int ES = (int)sizeof(TQ);
+    const float a0 = Ld1<TQ, ES * 32 * I>::f(ar), a1 = Ld1<TQ, ES * (32 * I + 1)>::f(ar);
+    const float smp = fmaf(f, a1 - a0, a0);
+    acc[0][I] = fmaf(w.x, smp, acc[0][I]);
+    acc[1][I] = fmaf(w.y, smp, acc[1][I]);
+    if (H == 2) {
+        acc[2][I] = fmaf(w.z, smp, acc[2][I]);
+        acc[3][I] = fmaf(w.w, smp, acc[3][I]);
     }
 }
 
-// off: the crop's offset inside its 16-byte aligned box (elements).  For
-// 16-bit data the vectors are 8 bytes, so the lane's address moves by whole
-// vectors and the remainder (0..3) picks the code path.
+template <typename TQ, int C, int H, int... I>
+__device__ __forceinline__ void row_cols(uint32_t ar, float f, float4 w, float (&acc)[2 * H][C],
+                                         std::integer_sequence<int, I...>) {
+    (col_step<TQ, I, C, H>(ar, f, w, acc), ...);
+}
+
 template <typename TQ, int C, int H, int RPL>
-__device__ __forceinline__ void view_step(uint32_t a, uint32_t rs, int off, float f, float4 w,
-                                          float (*acc)[2 * H][C]) {
-    if (sizeof(TQ) == 2) a += 8u * (uint32_t)(off >> 2);
-    switch (off & 3) {
-        case 0: view_cols<TQ, C, 0, H, RPL>(a, rs, f, w, acc); break;
-        case 1: view_cols<TQ, C, 1, H, RPL>(a, rs, f, w, acc); break;
-        case 2: view_cols<TQ, C, 2, H, RPL>(a, rs, f, w, acc); break;
-        default: view_cols<TQ, C, 3, H, RPL>(a, rs, f, w, acc); break;
-    }
+__device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, float4 w, float (&acc)[RPL][2 * H][C]) {
+#pragma unroll
+    for (int r = 0; r < RPL; ++r)
+        row_cols<TQ, C, H>(a + rs * (uint32_t)r, f, w, acc[r], std::make_integer_sequence<int, C>{});
 }
 
-template <typename TQ, int C, int LPR, int H>
+template <typename TQ, int C, int H>
 __global__ void __launch_bounds__(kDecThreads)
 decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ Sp,
                      const int32_t *__restrict__ crop, const GeomEntry *__restrict__ geo,
                      const int32_t *__restrict__ Tq, const float4 *__restrict__ tapw, int *status, int Tstride, int P,
-                     int D, int Pd, int Nv, int Wc, int tile_stride) {
+                     int D, int Pd, int Nv, int Wc, int tile_stride, int rowoff, int rowend) {
     constexpr int ES = (int)sizeof(TQ);
     constexpr int kAlign = 16 / ES;
     constexpr int kG = Ring<TQ>::kG, kStages = Ring<TQ>::kStages;
     constexpr int RPL = rows_per_lane(H);
-    constexpr int RPW = 32 / LPR * RPL;        // detector rows per consumer warp
-    constexpr int VB = kConsumerWarps * RPW;   // rows per CTA (box height)
+    constexpr int VB = kConsumerWarps * RPL;   // rows per CTA (box height)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ring = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
     const uint32_t tile_bytes = (uint32_t)(ES * tile_stride);
     // views streamed: k' = -(H D - 1) .. P - 1 + (H - 1) D (view k' mod P)
     const int nstream = P + (2 * H - 1) * D - 1;
     const int nstage = (nstream + kG - 1) / kG;
-    float4 *s_taps = (float4 *)(ring + (size_t)tile_bytes * kStages * kG + kRingSlack);
+    float4 *s_taps = (float4 *)(ring + (size_t)tile_bytes * kStages * kG + kColSlack(C));
     float2 *s_fc = (float2 *)(s_taps + D);
     int *s_c = (int *)(s_fc + nstream);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
 
     const int q = blockIdx.x;
-    const int v0 = blockIdx.y * VB;
+    const int v0 = rowoff + blockIdx.y * VB;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 
     build_stream_table<kAlign>(s_fc, s_c, s_taps, crop, geo, tapw, q, P, D, Pd, H);
@@ -305,12 +293,9 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
         return;
     }
 
-    const int rib = (ty * (32 / LPR) + tx / LPR) * RPL;  // first of the lane's rows in the band
-    const int t0 = (tx % LPR) * C;                      // first column of the lane
+    const int rib = ty * RPL;  // first of the warp's rows in the band
     const int v = v0 + rib;
     const int T = Tq[q];
-    const bool act = t0 < T;
-    const bool store = t0 < Tstride;
     float acc[RPL][2 * H][C];
 #pragma unroll
     for (int r = 0; r < RPL; ++r)
@@ -319,8 +304,8 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
 #pragma unroll
             for (int i = 0; i < C; ++i) acc[r][m][i] = 0.f;
     const size_t vstride = (size_t)Nv * Tstride;
-    float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + t0;  // row v; row v + r is r Tstride further
-    const uint32_t lane_addr = tma::smem_u32(ring) + (uint32_t)(ES * (rib * Wc + t0));
+    float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + tx;  // row v; row v + r is r Tstride further
+    const uint32_t lane_addr = tma::smem_u32(ring) + (uint32_t)(ES * (rib * Wc + tx));
     const uint32_t row_bytes = (uint32_t)(ES * Wc);
     int slot = 0;
     uint32_t phase = 0;
@@ -339,23 +324,18 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                 const float2 fc = s_fc[n * kG + w];
                 const int code = __float_as_int(fc.y);
                 const float4 tp = s_taps[(code >> kCodeTapShift) & 255];
-                if (act)
-                    view_step<TQ, C, H, RPL>(sa + tile_bytes * (uint32_t)w, row_bytes, code & (kAlign - 1), fc.x, tp,
-                                             acc);
+                view_cols<TQ, C, H, RPL>(sa + tile_bytes * (uint32_t)w + (uint32_t)(ES * (code & (kAlign - 1))),
+                                         row_bytes, fc.x, tp, acc);
                 if (code & kCodeRotate) {
                     const int jst = (code >> kCodeStoreShift) - 1;
-                    if (jst >= 0 && store) {
+                    if (jst >= 0) {
 #pragma unroll
                         for (int r = 0; r < RPL; ++r) {
-                            if (v + r < Nv) {
-                                float o[C];
+                            if (v + r < rowend) {
+                                float *dst = out + (size_t)jst * vstride + (size_t)r * Tstride;
 #pragma unroll
-                                for (int i = 0; i < C; ++i) o[i] = t0 + i < T ? acc[r][0][i] : 0.f;
-                                float4 *dst = (float4 *)(out + (size_t)jst * vstride + (size_t)r * Tstride);
-#pragma unroll
-                                for (int i = 0; i < C / 4; ++i)  // Tstride is a multiple of 4
-                                    if (t0 + 4 * i < Tstride)
-                                        dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                                for (int i = 0; i < C; ++i)
+                                    if (tx + 32 * i < Tstride) dst[32 * i] = tx + 32 * i < T ? acc[r][0][i] : 0.f;
                             }
                         }
                     }
@@ -379,37 +359,37 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     }
 }
 
-// columns per lane C and lanes per row LPR from the decomposed row length
-struct DecShape {
-    int C, LPR;
-};
-inline DecShape dec_shape(int Tstride) {
-    if (Tstride <= 32) return {4, 8};
-    if (Tstride <= 64) return {4, 16};
-    if (Tstride <= 128) return {4, 32};
-    return {8, 32};
-}
+// columns per lane C (lane t takes t, t + 32, ...) from the decomposed row length
+inline int dec_cols(int Tstride) { return Tstride <= 32 ? 1 : Tstride <= 64 ? 2 : Tstride <= 128 ? 4 : 8; }
 
-template <typename TQ, int C, int LPR, int H>
+// Rows of a launch: the arrays hold `layout` rows per view (S' included)
+// and the launch covers rows rowoff .. rowend - 1 of them.
+struct Rows {
+    int layout, rowoff, rowend;
+};
+
+template <typename TQ, int C, int H>
 cudaError_t launch_tma_shape(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st,
-                             int nrows, size_t smem, int tile_stride) {
-    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, LPR, H>>(smem);
+                             Rows rw, size_t smem, int tile_stride) {
+    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, H>>(smem);
     if (e != cudaSuccess) return e;
-    constexpr int VB = kConsumerWarps * (32 / LPR) * rows_per_lane(H);
-    dim3 grid(p.od.nsq, (nrows + VB - 1) / VB);
-    decompose_tma_kernel<TQ, C, LPR, H><<<grid, kDecThreads, smem, st>>>(map, out, p.od.crop, p.od.geo, p.od.T,
-                                                                         p.tapw, p.status, p.Tstride, p.g.P, p.D,
-                                                                         p.Pd, nrows, Wc, tile_stride);
+    constexpr int VB = kConsumerWarps * rows_per_lane(H);
+    dim3 grid(p.od.nsq, (rw.rowend - rw.rowoff + VB - 1) / VB);
+    decompose_tma_kernel<TQ, C, H><<<grid, kDecThreads, smem, st>>>(
+        map, out, p.od.crop, p.od.geo, p.od.T, p.tapw, p.status, p.Tstride, p.g.P, p.D, p.Pd, rw.layout, Wc,
+        tile_stride, rw.rowoff, rw.rowend);
     return cudaGetLastError();
 }
 
 template <typename TQ, int H>
-cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, int nrows,
-                         size_t smem, int tile_stride, DecShape sh) {
-    if (sh.C == 8) return launch_tma_shape<TQ, 8, 32, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    if (sh.LPR == 32) return launch_tma_shape<TQ, 4, 32, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    if (sh.LPR == 16) return launch_tma_shape<TQ, 4, 16, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
-    return launch_tma_shape<TQ, 4, 8, H>(p, map, out, Wc, st, nrows, smem, tile_stride);
+cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, Rows rw,
+                         size_t smem, int tile_stride) {
+    switch (dec_cols(p.Tstride)) {
+        case 1: return launch_tma_shape<TQ, 1, H>(p, map, out, Wc, st, rw, smem, tile_stride);
+        case 2: return launch_tma_shape<TQ, 2, H>(p, map, out, Wc, st, rw, smem, tile_stride);
+        case 4: return launch_tma_shape<TQ, 4, H>(p, map, out, Wc, st, rw, smem, tile_stride);
+        default: return launch_tma_shape<TQ, 8, H>(p, map, out, Wc, st, rw, smem, tile_stride);
+    }
 }
 
 // TMA applies when Q's rows are whole 16-byte units, Q and S' are 16-byte
@@ -417,17 +397,18 @@ cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, 
 // alignment) fits 256 columns, D <= 128 and the ring plus the stream tables
 // fit in shared memory.
 template <typename TQ>
-cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows, bool &launched) {
+cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, Rows rw, bool &launched) {
+    const int nrows = rw.layout;
     launched = false;
     constexpr int kAlign = 16 / (int)sizeof(TQ);
     if ((p.g.Nu % kAlign) != 0 || ((uintptr_t)Q & 15) != 0 || ((uintptr_t)out & 15) != 0) return cudaSuccess;
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
     if (Wc > 256 || p.Tstride > 256 || p.D > kMaxTapD) return cudaSuccess;  // block offset: 8 bits of the code
-    const DecShape sh = dec_shape(p.Tstride);
-    const int VB = kConsumerWarps * (32 / sh.LPR) * rows_per_lane(p.tap_blocks);
+    const int VB = kConsumerWarps * rows_per_lane(p.tap_blocks);
     const int tile_stride = (VB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
     const int nstream = p.g.P + (2 * p.tap_blocks - 1) * p.D - 1;
-    const size_t smem = 128 + sizeof(TQ) * (size_t)Ring<TQ>::kStages * Ring<TQ>::kG * tile_stride + kRingSlack +
+    const size_t smem = 128 + sizeof(TQ) * (size_t)Ring<TQ>::kStages * Ring<TQ>::kG * tile_stride +
+                        kColSlack(dec_cols(p.Tstride)) +
                         16 * (size_t)p.D +
                         12 * (size_t)nstream;
     if (smem > 200 * 1024) return cudaSuccess;
@@ -440,23 +421,25 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     if (encode_map_3d(&map, dt, Q, dims, strides, box) != cudaSuccess) return cudaSuccess;
     launched = true;
-    if (p.tap_blocks == 2) return launch_tma_h<TQ, 2>(p, map, out, Wc, st, nrows, smem, tile_stride, sh);
-    return launch_tma_h<TQ, 1>(p, map, out, Wc, st, nrows, smem, tile_stride, sh);
+    if (p.tap_blocks == 2) return launch_tma_h<TQ, 2>(p, map, out, Wc, st, rw, smem, tile_stride);
+    return launch_tma_h<TQ, 1>(p, map, out, Wc, st, rw, smem, tile_stride);
 }
 
 template <typename TQ>
-cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, int nrows) {
+cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st, Rows rw) {
     if (p.tap_blocks != 1 && p.tap_blocks != 2) return cudaErrorInvalidValue;
     bool launched = false;
-    cudaError_t te = try_tma(p, Q, out, st, nrows, launched);
+    cudaError_t te = try_tma(p, Q, out, st, rw, launched);
     if (launched || te != cudaSuccess) return te;
-    dim3 grid((p.Tstride + kTX - 1) / kTX, (nrows + kTY - 1) / kTY, p.od.nsq);
+    dim3 grid((p.Tstride + kTX - 1) / kTX, (rw.rowend - rw.rowoff + kTY - 1) / kTY, p.od.nsq);
     if (p.tap_blocks == 2)
         decompose_kernel<TQ, 2><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.tapw,
-                                                                 p.Tstride, p.g.P, p.D, p.Pd, nrows, p.g.Nu);
+                                                                 p.Tstride, p.g.P, p.D, p.Pd, rw.layout, p.g.Nu,
+                                                                 rw.rowoff, rw.rowend);
     else
         decompose_kernel<TQ, 1><<<grid, dim3(kTX, kTY), 0, st>>>(Q, out, p.od.crop, p.od.geo, p.od.T, p.tapw,
-                                                                 p.Tstride, p.g.P, p.D, p.Pd, nrows, p.g.Nu);
+                                                                 p.Tstride, p.g.P, p.D, p.Pd, rw.layout, p.g.Nu,
+                                                                 rw.rowoff, rw.rowend);
     return cudaGetLastError();
 }
 
@@ -464,11 +447,16 @@ cudaError_t launch_t(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st
 
 cudaError_t launch_decompose(const PlanImpl &p, const void *Q, float *out, cudaStream_t st, Band b) {
     const int nrows = b.nrows < 0 ? p.g.Nv : b.nrows;
-    if (p.net) return launch_net_decompose(p, Q, out, st, nrows);
+    Rows rw{nrows, 0, nrows};
+    if (b.whole_arrays) rw = Rows{p.g.Nv, b.row0, b.row0 + nrows};
+    if (p.net) {
+        if (b.whole_arrays && (b.row0 != 0 || nrows != p.g.Nv)) return cudaErrorInvalidValue;
+        return launch_net_decompose(p, Q, out, st, nrows);
+    }
     switch (p.qtype) {
-        case FDKOD_F32: return launch_t(p, (const float *)Q, out, st, nrows);
-        case FDKOD_BF16: return launch_t(p, (const __nv_bfloat16 *)Q, out, st, nrows);
-        case FDKOD_F16: return launch_t(p, (const __half *)Q, out, st, nrows);
+        case FDKOD_F32: return launch_t(p, (const float *)Q, out, st, rw);
+        case FDKOD_BF16: return launch_t(p, (const __nv_bfloat16 *)Q, out, st, rw);
+        case FDKOD_F16: return launch_t(p, (const __half *)Q, out, st, rw);
     }
     return cudaErrorInvalidValue;
 }

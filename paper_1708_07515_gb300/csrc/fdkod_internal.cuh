@@ -149,6 +149,10 @@ void tap_table(const double *h, int H, int D, float4 *w);
 // The defaults (nrows, nz < 0) mean the whole detector and volume.
 struct Band {
     int row0 = 0, nrows = -1, zoff = 0, nz = -1;
+    // the filter and the decomposition only: the arrays hold the whole
+    // detector ([P][Nv][...]) and the launch covers its rows row0 .. row0 +
+    // nrows - 1 (instead of arrays that hold just those rows)
+    bool whole_arrays = false;
 };
 
 // kernel launchers (return cudaError_t of the launch)

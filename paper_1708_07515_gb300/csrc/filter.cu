@@ -247,14 +247,26 @@ __device__ __forceinline__ void fft(float2 *buf, const float2 *tw, int lgL, int 
     else if (rest == 1) pass<2, OUT>(buf, tw, lgL, lgNs, lt, nt, sink);
 }
 
+// Where the launch's rows live: the arrays hold view_rows rows per view
+// (rows_per_view when they hold just the band, Nv for whole-detector
+// arrays), and band row i of view k sits at memory row k view_rows + off + i.
+struct RowMap {
+    int rows_per_view, view_rows, off;
+    __device__ __forceinline__ long long mem(long long r) const {
+        const long long k = r / rows_per_view;
+        return k * view_rows + off + (r - k * rows_per_view);
+    }
+};
+
 // G row pairs per CTA, L/16 threads per pair: weighted rows into shared
 // memory, forward transform (times the spectrum on its last pass), inverse
 // transform (its last pass stores the rows of Q).
 template <typename TQ>
 __global__ void __launch_bounds__(kThreads)
 filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
-              const float2 *__restrict__ tw, int L, int lgL, int G, int Nu, int Nv, int row0, int rows_per_view,
+              const float2 *__restrict__ tw, int L, int lgL, int G, int Nu, int Nv, int row0, RowMap rm,
               long long nrows, float R) {
+    const int rows_per_view = rm.rows_per_view;
     extern __shared__ float2 z[];
     const int nt = L / 16;
     const int g = threadIdx.x / nt, lt = threadIdx.x % nt;
@@ -270,16 +282,16 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
         float2 v = make_float2(0.f, 0.f);
         if (i < Nu) {
             const float u = (float)i - 0.5f * (float)(Nu - 1);
-            if (hasA) v.x = __ldg(proj + rowA * Nu + i) * (R * rsqrtf(R2 + u * u + bA * bA));
-            if (hasB) v.y = __ldg(proj + rowB * Nu + i) * (R * rsqrtf(R2 + u * u + bB * bB));
+            if (hasA) v.x = __ldg(proj + rm.mem(rowA) * Nu + i) * (R * rsqrtf(R2 + u * u + bA * bA));
+            if (hasB) v.y = __ldg(proj + rm.mem(rowB) * Nu + i) * (R * rsqrtf(R2 + u * u + bB * bB));
         }
         buf[pad(i)] = v;
     }
     __syncthreads();
     Sink<TQ> sink;
     sink.H = H;
-    sink.qa = hasA ? Q + rowA * Nu : nullptr;
-    sink.qb = hasB ? Q + rowB * Nu : nullptr;
+    sink.qa = hasA ? Q + rm.mem(rowA) * Nu : nullptr;
+    sink.qb = hasB ? Q + rm.mem(rowB) * Nu : nullptr;
     sink.Nu = Nu;
     fft<kToSpectrum>(buf, tw, lgL, lt, nt, sink);
     fft<kToQ>(buf, tw, lgL, lt, nt, sink);
@@ -341,8 +353,9 @@ constexpr size_t kFilterSmem =
 template <typename TQ>
 __global__ void __launch_bounds__(32 * kFilterWarps, 3)
 filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *__restrict__ H,
-                   const float2 *__restrict__ tw2, int Nu, int Nv, int row0, int rows_per_view, int nrows, float R,
+                   const float2 *__restrict__ tw2, int Nu, int Nv, int row0, RowMap rm, int nrows, float R,
                    int *status) {
+    const int rows_per_view = rm.rows_per_view;
     extern __shared__ __align__(128) unsigned char fsm_raw[];
     unsigned char *base = fsm_raw + ((128u - (tma::smem_u32(fsm_raw) & 127u)) & 127u);
     float(*stg)[kStage] = reinterpret_cast<float(*)[kStage]>(base);
@@ -364,13 +377,19 @@ filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const flo
     const int stride = gridDim.x * kFilterWarps;
     float *in = stg[warp];
     float2 *t = tile[warp];
-    // rows 2 pr and 2 pr + 1 are adjacent in memory: one copy
+    // rows 2 pr and 2 pr + 1: one copy where they are adjacent in memory
     auto stage = [&](int pr) {
         const int rows = min(2, nrows - 2 * pr);
-        const uint32_t bytes = (uint32_t)(rows * Nu) * 4u;
+        const long long ma = rm.mem(2 * pr), mb = rm.mem(2 * pr + 1);
+        const uint32_t row_bytes = (uint32_t)Nu * 4u;
         tma::fence_proxy_async();
-        tma::mbar_arrive_expect_tx(&bar[warp], bytes);
-        tma::bulk_load(in, proj + (size_t)(2 * pr) * Nu, bytes, &bar[warp]);
+        tma::mbar_arrive_expect_tx(&bar[warp], (uint32_t)rows * row_bytes);
+        if (rows == 2 && mb != ma + 1) {
+            tma::bulk_load(in, proj + (size_t)ma * Nu, row_bytes, &bar[warp]);
+            tma::bulk_load(in + Nu, proj + (size_t)mb * Nu, row_bytes, &bar[warp]);
+        } else {
+            tma::bulk_load(in, proj + (size_t)ma * Nu, (uint32_t)rows * row_bytes, &bar[warp]);
+        }
     };
     int pair = blockIdx.x * kFilterWarps + warp;
     if (pair < npairs && lane == 0) stage(pair);
@@ -435,7 +454,7 @@ filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const flo
             }
         }
         // sample n = lane + 32 n2 of the conjugated result: row A real, row B imaginary
-        TQ *qa = Q + (size_t)rowA * Nu, *qb = qa + Nu;
+        TQ *qa = Q + (size_t)rm.mem(rowA) * Nu, *qb = Q + (size_t)rm.mem(rowB) * Nu;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) {
             const int n = lane + 32 * n2;
@@ -450,8 +469,12 @@ filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const flo
 
 template <typename TQ>
 cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t st, int row0, int rows_per_view,
-                     int views) {
+                     int views, bool whole_arrays) {
     const long long nrows = (long long)views * rows_per_view;
+    RowMap rm;
+    rm.rows_per_view = rows_per_view;
+    rm.view_rows = whole_arrays ? p.g.Nv : rows_per_view;
+    rm.off = whole_arrays ? row0 : 0;
     const long long pairs = (nrows + 1) / 2;
     // the warp form stages rows with bulk copies: 16-byte aligned rows
     if (p.L == 1024 && p.tw2 && (p.g.Nu % 4) == 0 && ((uintptr_t)proj & 15) == 0 && nrows < (1LL << 30)) {
@@ -468,7 +491,7 @@ cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t s
         const long long need = (pairs + kFilterWarps - 1) / kFilterWarps;
         const long long blocks = std::max(1LL, std::min(need, (long long)std::max(1, per_sm) * sms));
         filter_1024_kernel<TQ><<<(unsigned)blocks, 32 * kFilterWarps, smem, st>>>(
-            proj, Q, p.H, p.tw2, p.g.Nu, p.g.Nv, row0, rows_per_view, (int)nrows, (float)p.g.R, p.status);
+            proj, Q, p.H, p.tw2, p.g.Nu, p.g.Nv, row0, rm, (int)nrows, (float)p.g.R, p.status);
         return cudaGetLastError();
     }
     const int G = std::max(1, 2048 / p.L);  // 128 threads per CTA up to L = 2048
@@ -477,7 +500,7 @@ cudaError_t launch_t(const PlanImpl &p, const float *proj, TQ *Q, cudaStream_t s
     cudaError_t e = ensure_smem<filter_kernel<TQ>>(smem);
     if (e != cudaSuccess) return e;
     filter_kernel<TQ><<<(unsigned)blocks, G * (p.L / 16), smem, st>>>(proj, Q, p.H, p.tw, p.L, p.log2L, G, p.g.Nu, p.g.Nv,
-                                                                      row0, rows_per_view, nrows, (float)p.g.R);
+                                                                      row0, rm, nrows, (float)p.g.R);
     return cudaGetLastError();
 }
 
@@ -488,9 +511,9 @@ cudaError_t launch_filter(const PlanImpl &p, const float *proj, void *Q, cudaStr
     if (views < 0) views = p.g.P;
     if (views == 0) return cudaSuccess;
     switch (p.qtype) {
-        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st, b.row0, rows, views);
-        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st, b.row0, rows, views);
-        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st, b.row0, rows, views);
+        case FDKOD_F32: return launch_t(p, proj, (float *)Q, st, b.row0, rows, views, b.whole_arrays);
+        case FDKOD_BF16: return launch_t(p, proj, (__nv_bfloat16 *)Q, st, b.row0, rows, views, b.whole_arrays);
+        case FDKOD_F16: return launch_t(p, proj, (__half *)Q, st, b.row0, rows, views, b.whole_arrays);
     }
     return cudaErrorInvalidValue;
 }

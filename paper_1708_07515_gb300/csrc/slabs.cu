@@ -135,22 +135,30 @@ extern "C" int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_hos
 // plan keeps device buffers for the projections, the filtered projections
 // and the volume, plus an upload and a read-back stream (made on the first
 // call).  Within one call
-//   - the projections go up in chunks of views on the upload stream, and
-//     the compute stream filters each chunk as soon as it has landed;
-//   - the bounds, the decomposition and the backprojection run on the
-//     compute stream once every view is filtered;
-//   - the backprojection runs in z-slabs, and each slab's read-back on the
-//     read-back stream overlaps the next slab's backprojection.
+//   - the projections go up in bands of detector rows (every view) on the
+//     upload stream, and the compute stream filters and decomposes each band
+//     as soon as it has landed (both stages are row-local);
+//   - the backprojection runs once every band is decomposed, in groups of
+//     slice pairs, and each group's read-back on the read-back stream
+//     overlaps the next group's backprojection.
 namespace fdkod {
 
-constexpr int kPipeChunks = 8;  // view chunks of the upload
-constexpr int kPipeSlabs = 4;   // z-slabs of the backprojection / read-back
+// Four row bands: the strided copy of a band (one segment per view) keeps
+// near the contiguous copy rate down to about 256 KiB segments (measured:
+// 211 GB/s for two bands of 512^2 x 720 float32, 185 for four, 127 for eight).
+constexpr int kPipeChunks = 4;  // row bands of the upload
+constexpr int kPipeSlabs = 8;   // groups of slice pairs of the backprojection / read-back
 
+// The bands are filtered and decomposed on a stream of their own (in upload
+// order), and the groups' backprojections alternate between the caller's
+// stream and a third one: a group fills only part of the GPU, and launches
+// on one stream cannot overlap their last partial wave with the next launch.
 struct HostPipe {
     float *proj = nullptr, *vol = nullptr;
     void *Q = nullptr;
-    cudaStream_t up = nullptr, down = nullptr;
-    cudaEvent_t ev_up[kPipeChunks] = {}, ev_slab[kPipeSlabs] = {}, ev_start = nullptr;
+    cudaStream_t up = nullptr, down = nullptr, comp2 = nullptr, comp3 = nullptr;
+    cudaEvent_t ev_up[kPipeChunks] = {}, ev_band[kPipeChunks] = {}, ev_slab[kPipeSlabs] = {};
+    cudaEvent_t ev_start = nullptr, ev_join = nullptr;
     int64_t bytes = 0;
 };
 
@@ -158,13 +166,20 @@ void free_host_pipe(HostPipe *hp) {
     if (!hp) return;
     if (hp->up) cudaStreamSynchronize(hp->up);
     if (hp->down) cudaStreamSynchronize(hp->down);
+    if (hp->comp2) cudaStreamSynchronize(hp->comp2);
+    if (hp->comp3) cudaStreamSynchronize(hp->comp3);
     for (cudaEvent_t e : hp->ev_up)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : hp->ev_band)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : hp->ev_slab)
         if (e) cudaEventDestroy(e);
     if (hp->ev_start) cudaEventDestroy(hp->ev_start);
+    if (hp->ev_join) cudaEventDestroy(hp->ev_join);
     if (hp->up) cudaStreamDestroy(hp->up);
     if (hp->down) cudaStreamDestroy(hp->down);
+    if (hp->comp2) cudaStreamDestroy(hp->comp2);
+    if (hp->comp3) cudaStreamDestroy(hp->comp3);
     cudaFree(hp->proj);
     cudaFree(hp->Q);
     cudaFree(hp->vol);
@@ -188,15 +203,19 @@ cudaError_t make_pipe(PlanImpl &p, fdkod::HostPipe **out) {
         (e = cudaMalloc(&hp->vol, sizeof(float) * voxels)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&hp->up, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&hp->down, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&hp->ev_start, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&hp->comp2, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&hp->comp3, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&hp->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&hp->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
         fdkod::free_host_pipe(hp);
         return e;
     }
-    for (auto &ev : hp->ev_up)
-        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
-            fdkod::free_host_pipe(hp);
-            return e;
-        }
+    for (cudaEvent_t *evs : {hp->ev_up, hp->ev_band})
+        for (int i = 0; i < fdkod::kPipeChunks; ++i)
+            if ((e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming)) != cudaSuccess) {
+                fdkod::free_host_pipe(hp);
+                return e;
+            }
     for (auto &ev : hp->ev_slab)
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
             fdkod::free_host_pipe(hp);
@@ -224,48 +243,87 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
     fdkod::HostPipe &hp = *p.pipe;
     const int N = p.g.N, Nv = p.g.Nv, Nu = p.g.Nu, P = p.g.P;
     const size_t view = (size_t)Nv * Nu;
-    const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
     cudaStream_t comp = (cudaStream_t)stream;
     // the previous call's work on the compute stream (and the caller's) comes first
     SLAB_TRY(cudaEventRecord(hp.ev_start, comp));
     SLAB_TRY(cudaStreamWaitEvent(hp.up, hp.ev_start, 0));
-    // upload in chunks of an even number of views (the filter pairs rows in
-    // one complex transform; even chunk starts keep the whole-array pairing)
-    int cv = (P + kPipeChunks - 1) / kPipeChunks;
-    cv += cv & 1;
-    int nch = 0;
-    for (int k0 = 0; k0 < P; k0 += cv, ++nch) {
-        const int nv = std::min(cv, P - k0);
-        SLAB_TRY(cudaMemcpyAsync(hp.proj + (size_t)k0 * view, proj_host + (size_t)k0 * view,
-                                 sizeof(float) * view * nv, cudaMemcpyHostToDevice, hp.up));
-        SLAB_TRY(cudaEventRecord(hp.ev_up[nch], hp.up));
+    SLAB_TRY(cudaStreamWaitEvent(hp.comp2, hp.ev_start, 0));
+    SLAB_TRY(cudaStreamWaitEvent(hp.comp3, hp.ev_start, 0));
+    cudaStream_t cs[2] = {comp, hp.comp3};  // backprojection groups
+    // upload in bands of detector rows (every view, one strided copy per
+    // band), outermost bands first; the filter and the decomposition are
+    // row-local, so each band is filtered and decomposed as soon as it has
+    // landed.  A slice pair (p, N - 1 - p) reads rows near both edges of the
+    // detector (row z/U + (Nv-1)/2, Sec. 2.2), so the outermost pairs can be
+    // backprojected once the two outer bands are done, while the inner bands
+    // are still on their way.  Bands hold an even number of rows from an even
+    // first row (the filter pairs rows in one complex transform, as the
+    // whole-detector launch does); an odd Nv, or a learned decimation (its
+    // kernel takes every row at once), makes one band.
+    const bool banded = (Nv % 2) == 0 && !p.net;
+    int rb = banded ? (Nv + kPipeChunks - 1) / kPipeChunks : Nv;
+    rb += rb & 1;
+    const int nbands = (Nv + rb - 1) / rb;
+    int order[kPipeChunks];  // outside in: 0, last, 1, last - 1, ...
+    for (int i = 0, lo = 0, hi = nbands - 1; i < nbands; ++i) order[i] = (i & 1) ? hi-- : lo++;
+    const size_t pitch = sizeof(float) * view;
+    for (int i = 0; i < nbands; ++i) {
+        const int v0 = order[i] * rb, nb = std::min(rb, Nv - v0);
+        SLAB_TRY(cudaMemcpy2DAsync(hp.proj + (size_t)v0 * Nu, pitch, proj_host + (size_t)v0 * Nu, pitch,
+                                   sizeof(float) * (size_t)nb * Nu, (size_t)P, cudaMemcpyHostToDevice, hp.up));
+        SLAB_TRY(cudaEventRecord(hp.ev_up[order[i]], hp.up));
     }
     SLAB_TRY(fdkod::launch_bounds(p, p.od, comp));
-    nch = 0;
-    for (int k0 = 0; k0 < P; k0 += cv, ++nch) {
-        const int nv = std::min(cv, P - k0);
-        SLAB_TRY(cudaStreamWaitEvent(comp, hp.ev_up[nch], 0));
-        SLAB_TRY(fdkod::launch_filter(p, hp.proj + (size_t)k0 * view, (char *)hp.Q + es * (size_t)k0 * view, comp,
-                                      fdkod::Band{}, nv));
+    SLAB_TRY(cudaEventRecord(hp.ev_join, comp));
+    SLAB_TRY(cudaStreamWaitEvent(hp.comp2, hp.ev_join, 0));  // the bounds before any decomposition
+    for (int i = 0; i < nbands; ++i) {
+        const int bi = order[i];
+        fdkod::Band rows;
+        rows.row0 = bi * rb;
+        rows.nrows = std::min(rb, Nv - rows.row0);
+        rows.whole_arrays = true;
+        cudaStream_t c = hp.comp2;
+        SLAB_TRY(cudaStreamWaitEvent(c, hp.ev_up[bi], 0));
+        SLAB_TRY(fdkod::launch_filter(p, hp.proj, hp.Q, c, rows));
+        if (p.D > 1 && banded) SLAB_TRY(fdkod::launch_decompose(p, hp.Q, p.Sp, c, rows));
+        SLAB_TRY(cudaEventRecord(hp.ev_band[bi], c));
     }
-    if (p.D > 1) SLAB_TRY(fdkod::launch_decompose(p, hp.Q, p.Sp, comp));
+    if (p.D > 1 && !banded) {
+        SLAB_TRY(fdkod::launch_decompose(p, hp.Q, p.Sp, hp.comp2));
+        SLAB_TRY(cudaEventRecord(hp.ev_band[0], hp.comp2));
+    }
+    // make stream c wait for the bands holding detector rows that slices
+    // z0 .. z0 + nz - 1 can read (the bound of fdkod_slab_rows)
+    auto wait_rows = [&](cudaStream_t c, int z0, int nz) -> int {
+        int32_t v0 = 0, nr = 0;
+        const int rc = fdkod_slab_rows(plan, z0, nz, &v0, &nr);
+        if (rc != FDKOD_OK) return rc;
+        for (int bi = 0; bi < nbands; ++bi)
+            if (bi * rb < v0 + nr && (bi + 1) * rb > v0) SLAB_TRY(cudaStreamWaitEvent(c, hp.ev_band[bi], 0));
+        return FDKOD_OK;
+    };
     const bool direct = p.D == 1;
     const void *src = direct ? hp.Q : (const void *)p.Sp;
     // backprojection in groups of slice pairs (slices p and N - 1 - p, the
-    // same tiles as one whole-volume launch); each group's two z-ranges are
-    // read back while the next group is computed
+    // same tiles as one whole-volume launch), outermost first, alternating
+    // between the two compute streams, each after the bands it reads; each
+    // group's two z-ranges are read back as soon as it is done
     const int npair = (N + 1) / 2;
     int ps = (npair + kPipeSlabs - 1) / kPipeSlabs;
     ps = (ps + fdkod::kZP - 1) / fdkod::kZP * fdkod::kZP;
     int ns = 0;
     bool paired = true;
+    const size_t plane = (size_t)N * N;
     for (int pa = 0; pa < npair && paired; pa += ps, ++ns) {
         const int pb = std::min(pa + ps, npair);
-        SLAB_TRY(fdkod::launch_backproject_pairs(p, p.od, direct, src, hp.vol, comp, pa, pb, paired));
+        cudaStream_t c = cs[ns & 1];
+        int rc = wait_rows(c, pa, pb - pa);
+        if (rc == FDKOD_OK) rc = wait_rows(c, N - pb, pb - pa);
+        if (rc != FDKOD_OK) return rc;
+        SLAB_TRY(fdkod::launch_backproject_pairs(p, p.od, direct, src, hp.vol, c, pa, pb, paired));
         if (!paired) break;  // not staged: z-slabs below (before anything was launched)
-        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], comp));
+        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], c));
         SLAB_TRY(cudaStreamWaitEvent(hp.down, hp.ev_slab[ns], 0));
-        const size_t plane = (size_t)N * N;
         SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)pa * plane, hp.vol + (size_t)pa * plane,
                                  sizeof(float) * (size_t)(pb - pa) * plane, cudaMemcpyDeviceToHost, hp.down));
         const int u0 = std::max(N - pb, pb), u1 = N - pa;  // upper slices, the middle one (odd N) once
@@ -273,6 +331,11 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
             SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)u0 * plane, hp.vol + (size_t)u0 * plane,
                                      sizeof(float) * (size_t)(u1 - u0) * plane, cudaMemcpyDeviceToHost, hp.down));
     }
+    if (!paired)  // the z-slab fallback reads every band
+        for (int bi = 0; bi < nbands; ++bi) {
+            SLAB_TRY(cudaStreamWaitEvent(comp, hp.ev_band[bi], 0));
+            SLAB_TRY(cudaStreamWaitEvent(hp.comp3, hp.ev_band[bi], 0));
+        }
     // z-slabs of whole 32-slice tiles where the staged pair kernel does not apply
     int zs = (N + kPipeSlabs - 1) / kPipeSlabs;
     zs = (zs + fdkod::kZT - 1) / fdkod::kZT * fdkod::kZT;
@@ -281,13 +344,16 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
         fdkod::Band b;
         b.zoff = z0;
         b.nz = std::min(zs, N - z0);
-        float *dst = hp.vol + (size_t)z0 * N * N;
-        SLAB_TRY(fdkod::launch_backproject(p, p.od, direct, src, dst, comp, b));
-        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], comp));
+        float *dst = hp.vol + (size_t)z0 * plane;
+        cudaStream_t c = cs[ns & 1];
+        SLAB_TRY(fdkod::launch_backproject(p, p.od, direct, src, dst, c, b));
+        SLAB_TRY(cudaEventRecord(hp.ev_slab[ns], c));
         SLAB_TRY(cudaStreamWaitEvent(hp.down, hp.ev_slab[ns], 0));
-        SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)z0 * N * N, dst, sizeof(float) * (size_t)b.nz * N * N,
+        SLAB_TRY(cudaMemcpyAsync(vol_host + (size_t)z0 * plane, dst, sizeof(float) * (size_t)b.nz * plane,
                                  cudaMemcpyDeviceToHost, hp.down));
     }
+    SLAB_TRY(cudaStreamSynchronize(hp.comp2));
+    SLAB_TRY(cudaStreamSynchronize(hp.comp3));
     SLAB_TRY(cudaStreamSynchronize(hp.down));
     SLAB_TRY(cudaStreamSynchronize(comp));
     return fdkod_last_device_status(plan, stream);

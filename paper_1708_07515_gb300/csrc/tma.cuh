@@ -95,6 +95,22 @@ __device__ __forceinline__ bool mbar_wait_spin(uint64_t *bar, uint32_t parity, u
     }
 }
 
+// The same wait for warps that share their SM sub-partition with warps that
+// have work: between polls (mbarrier.test_wait) the warp sleeps
+// (nanosleep, 32 ns doubling up to 512 ns), so a waiting warp issues a
+// handful of instructions instead of retrying at full rate.  False on timeout.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    uint32_t ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (mbar_test_wait(bar, parity)) return true;
+        if (ns < 512) ns <<= 1;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // 3D tiled bulk copy global -> shared, completion counted on `bar`.
 // x (innermost) must be a multiple of 16 bytes' worth of elements.
 __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {

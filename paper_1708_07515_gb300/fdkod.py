@@ -542,8 +542,9 @@ def _host_ptr(a, what, shape):
 def reconstruct(plan: Plan, proj_host, out=None, stream=None):
     """One whole reconstruction from host memory through fdkod_reconstruct:
     filter, bounds, FDK-OD backprojection, with the upload of the
-    projections (in chunks of views) and the read-back of the volume (in
-    z-slabs) overlapping the compute.  proj_host: float32 [P][Nv][Nu]
+    projections (in bands of detector rows, each filtered and decomposed as
+    it lands) and the read-back of the volume (in groups of slices)
+    overlapping the compute.  proj_host: float32 [P][Nv][Nu]
     (numpy or torch CPU; page-locked memory lets the copies overlap); returns
     the float32 [N][N][N] volume (numpy, or `out`, numpy or torch CPU)."""
     N = plan.N

@@ -1,6 +1,6 @@
 """Edge cases of the GPU path against the FP64 oracle: the smallest volumes
-(one voxel, squares of one voxel), the widest detector the filter takes
-(Nu = 2048), a source just outside the volume's circumscribed cylinder and
+(one voxel, squares of one voxel), wide detectors up to the widest the
+filter takes (Nu = 8192), a source just outside the volume's circumscribed cylinder and
 a nearly parallel beam, one view; plans that must be rejected or that run
 out of device memory; two plans working concurrently.  Bars as in
 test_gpu_parity.py."""
@@ -68,17 +68,20 @@ def test_extreme_source_distances(fd, oracle_mod, R):
     _cmp(pl, oracle_mod.fdk(Q, R, N), f"plain FDK R={R:.1f}")
 
 
-def test_widest_detector_filter(fd, oracle_mod):
-    """Nu = 2048 (L = 4096, 256 threads per row pair)."""
-    N, Nu, Nv, P = 64, 2048, 6, 3
+@pytest.mark.parametrize("Nu,L", [(2048, 4096), (2500, 8192), (8192, 16384)])
+def test_widest_detector_filter(fd, oracle_mod, Nu, L):
+    """Wide detectors up to the limit: Nu = 2048 (L = 4096, 256 threads per
+    row pair), 2500 (the widest the paper's experiments reach, L = 8192) and
+    8192 (L = 16384, 1024 threads per row pair)."""
+    N, Nv, P = 64, 6, 3
     R = 4.0 * N
     proj = np.random.default_rng(820).uniform(0.0, 1.0, (P, Nv, Nu)).astype(np.float32)
     with fd.Plan(R, N, Nu, Nv, P, 0, 1) as plan:
+        assert plan.info["fft_length"] == L
         Q = plan.filter(torch.from_numpy(proj).cuda()).cpu().numpy()
     want = oracle_mod.filter(proj, R)
     # FFT round-off bar of test_gpu_parity.py: 2 log2(L) 2^-24 times the norm
     # of the cosine-weighted row pair sharing one transform
-    L = 4096
     a = np.arange(Nu) - (Nu - 1) / 2
     b = np.arange(Nv) - (Nv - 1) / 2
     q = proj.astype(np.float64) * (R / np.sqrt(R * R + a[None, :] ** 2 + b[:, None] ** 2))[None]
@@ -90,7 +93,7 @@ def test_widest_detector_filter(fd, oracle_mod):
 
 def test_rejected_plans(fd):
     for args in [(10.0, 16, 16, 16, 8, 1, 1),     # source inside the volume
-                 (64.0, 16, 4096, 16, 8, 1, 1),   # detector wider than the filter takes
+                 (64.0, 16, 8200, 16, 8, 1, 1),   # detector wider than the filter takes
                  (64.0, 16, 16, 16, 8, 1, 3)]:    # D does not divide P
         with pytest.raises(fd.FdkodError) as e:
             fd.Plan(*args)

@@ -1,10 +1,10 @@
 """Whole reconstruction from host buffers (fdkod_reconstruct): projections
 in host memory, volume in host memory, the copies overlapped with the
 filter and the backprojection inside the call.  It runs the same kernels as
-the device-buffer entry points, in view chunks (filter) and z-slabs
-(backprojection) that keep their operand pairings, so its volume equals
-fdkod_filter + fdkod_backproject bit for bit; and it meets the FP64
-oracle at the parity bar."""
+the device-buffer entry points, in bands of detector rows (filter,
+decomposition) and groups of slices (backprojection) that keep their operand
+pairings, so its volume equals fdkod_filter + fdkod_backproject bit for bit
+(even Nv); and it meets the FP64 oracle at the parity bar."""
 import numpy as np
 import pytest
 
@@ -44,6 +44,20 @@ def test_host_buffer_reconstruction_equals_the_device_path(fd, oracle_mod, N, P,
         ref = oracle_mod.fdkod(oracle_mod.filter(proj, R), R, N, s, D)
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert rel <= 1e-5, rel
+
+
+def test_host_buffer_reconstruction_with_an_odd_detector_height(fd, oracle_mod):
+    """Nv odd: one band of rows (the filter's row pairs then match the
+    whole-detector launch's only up to FFT round-off)."""
+    N, Nu, Nv, P, s, D = 48, 52, 47, 60, 2, 3
+    R = 4.0 * N
+    proj = phantom.project(phantom.make_phantom(5300, N, 8), R, Nu, Nv, P)
+    with fd.Plan(R, N, Nu, Nv, P, s, D) as plan:
+        want = plan.backproject(plan.filter(torch.from_numpy(proj).cuda())).cpu().numpy()
+        got = fd.reconstruct(plan, proj)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-6
+    ref = oracle_mod.fdkod(oracle_mod.filter(proj, R), R, N, s, D)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
 def test_host_buffer_reconstruction_needs_the_workspace(fd):
