@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--persistent", action="store_true",
                     help="batched form: all volumes' backprojections in one persistent launch (after every "
                          "decomposition) instead of one launch per volume on its stream")
+    ap.add_argument("--split", choices=["scans", "z"], default="scans",
+                    help="with several ranks: each reconstructs its own scan (weak scaling), or one volume is split "
+                         "into z-slabs, each rank holding only the detector rows its slab reads (strong scaling)")
     ap.add_argument("--slabs", type=int, default=0,
                     help="slab-wise (piecemeal, Sec. 2.2) reconstruction from host buffers, this many slices per slab")
     ap.add_argument("--qtype", choices=["f32", "bf16", "f16"], default="f32",
@@ -421,6 +424,121 @@ def slabs_main(args):
     return 0
 
 
+def split_main(args):
+    """One volume split into z-slabs over the ranks (Sec. 2.2: a slab of
+    slices reads only the detector rows the row formula b = z R / (R + x cos
+    b + y sin b) allows).  Rank r reconstructs slab_partition(N, world)[r]
+    from that band of rows alone (filter_rows + backproject_slab, the
+    slab-wise entry points), with no exchange; the only collective is the max
+    of the timings.  Strong scaling: the units are the whole volume's N^3 P
+    effective updates, timed by the slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1708_07515_gb300 as fd
+    import phantom
+    from paper_1708_07515_gb300 import shard
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = phantom.WORKLOADS[args.workload]
+    z0, z1 = shard.slab_partition(w.N, world)[rank]
+    nz = z1 - z0
+    # the same scan on every rank (same seeds); each keeps only its band of rows
+    ell = phantom.make_phantom(w.seed, w.N, w.n_ell)
+    plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, workspace=False)
+    v0, nrows = plan.slab_rows(z0, max(nz, 1))
+    if w.noise and w.N <= 512:
+        # the whole noisy scan (seeded), so the overlapping bands of two ranks agree
+        full = phantom.make_projections(w)
+        band = np.ascontiguousarray(full[:, v0:v0 + nrows])
+        del full
+    else:
+        band = phantom.project(ell, w.R, w.Nu, w.Nv, w.P, rows=(v0, v0 + nrows))
+    proj_d = torch.from_numpy(band).cuda()
+    Qb = torch.empty(tuple(proj_d.shape), dtype=plan.q_torch_dtype, device="cuda")
+    S_work = torch.empty(max(1, plan.slab_workspace_elems(nrows)), dtype=torch.float32, device="cuda")
+    vol = torch.empty((max(nz, 1), w.N, w.N), dtype=torch.float32, device="cuda")
+
+    def step():
+        if nz > 0:
+            plan.filter_rows(proj_d, v0, Qb)
+            plan.backproject_slab(Qb, v0, S_work if w.D > 1 else None, z0, nz, vol)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    assert plan.device_status() == 0
+    from paper_1708_07515_gb300.shard import max_over_ranks
+    ms_step = max_over_ranks(t0.elapsed_time(t1)) / args.steps
+    value = float(w.N) ** 3 * w.P / (ms_step * 1e-3)
+    # end to end: the band up from page-locked host memory, the slab back
+    band_h = torch.from_numpy(band).pin_memory()
+    vol_h = torch.empty(tuple(vol.shape), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        proj_d.copy_(band_h, non_blocking=True)
+        step()
+        vol_h.copy_(vol, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    n_e2e = max(2, min(args.steps, 10))
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks((time.perf_counter() - a) * 1e3) / n_e2e
+    extra = {}
+    if rank == 0 and nz > 0:
+        import oracle
+        oracle.build()
+        zs = [z0, z0 + nz // 2, z1 - 1]
+        Qo = np.zeros((w.P, w.Nv, w.Nu))
+        Qo[:, v0:v0 + nrows] = oracle.filter_fft(band, w.R, v0=v0, Nv_det=w.Nv)
+        ref = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs)
+        got = vol[torch.as_tensor([z - z0 for z in zs], device="cuda")].cpu().numpy().astype(np.float64)
+        extra["rel_rmse_vs_fp64_fdkod_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        extra["accuracy_slices"] = zs
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded random-ellipsoid phantom, exact cone-beam projections"
+                    + (f", {100 * w.noise:g}% Gaussian noise" if w.noise and w.N <= 512 else ""),
+            "config": {**workload_config(w, args.qtype), "parallelism": f"one volume in {world} z-slabs",
+                       "step": "per rank: filter its band of detector rows, decompose and backproject its slab",
+                       "rank0_slab": [z0, z1], "rank0_rows": [v0, v0 + nrows]},
+            "e2e": {"value": float(w.N) ** 3 * w.P / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": band.nbytes, "d2h_bytes_per_step": nz * w.N * w.N * 4,
+                    "ms_per_step": ms_e2e, "note": "rank 0's band and slab; torch copies around the C ABI calls"},
+            "gpu_launches": args.steps * (2 + (1 if w.D > 1 else 0)), "clocks": clk.summary(), **extra}),
+            flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -429,6 +547,8 @@ def main():
         return batched_main(args)
     if args.slabs > 0:
         return slabs_main(args)
+    if args.split == "z":
+        return split_main(args)
     import torch
     import torch.distributed as dist
 
@@ -472,7 +592,7 @@ def main():
         taps = learn.learn(w.R, w.N, w.P, w.s, w.D, 2, train, zs_fit)
         del train
     net_w = net_src = None
-    if taps == "net":
+    if args.taps == "net":
         net_w, net_src = net_weights(args.net_weights, w.D)
         taps = "triangle"
     plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=taps)
@@ -482,7 +602,6 @@ def main():
     stream = torch.cuda.current_stream()
     proj_d = torch.from_numpy(proj).cuda()
     Q = torch.empty((w.P, w.Nv, w.Nu), dtype=plan.q_torch_dtype, device="cuda")
-    S = torch.empty((info["n_squares"], info["Pd"], w.Nv, info["T_stride"]), dtype=torch.float32, device="cuda")
     vol = torch.empty((w.N, w.N, w.N), dtype=torch.float32, device="cuda")
     upd_eff = float(w.N) ** 3 * w.P
 
@@ -495,10 +614,10 @@ def main():
         plan.filter(proj_d, Q)
         if ev is not None:
             ev[2].record(stream)
-        plan.decompose(Q, S)
+        plan.decompose_to_workspace(Q)  # the decomposed data stays in the plan's own workspace
         if ev is not None:
             ev[3].record(stream)
-        plan.backproject_decomposed(S, vol)
+        plan.backproject_decomposed_workspace(vol)
         if ev is not None:
             ev[4].record(stream)
 
@@ -561,14 +680,16 @@ def main():
         vol_h = torch.empty((w.N, w.N, w.N), dtype=torch.float32).pin_memory()
         for _ in range(max(2, min(args.warmup, 3))):
             fd.reconstruct(plan, proj_h, vol_h)
-        n_e2e = max(2, min(args.steps, 10))
+        n_e2e = max(2, min(args.steps, 30))
         barrier()
         torch.cuda.synchronize()
+        t_calls = []
         t_e0 = time.perf_counter()
         for _ in range(n_e2e):
             fd.reconstruct(plan, proj_h, vol_h)
-        t_e1 = time.perf_counter()
-        ms_e2e = max_over_ranks((t_e1 - t_e0) * 1e3) / n_e2e
+            t_calls.append(time.perf_counter())
+        ms_e2e = max_over_ranks((t_calls[-1] - t_e0) * 1e3) / n_e2e
+        ms_calls = np.diff([t_e0] + t_calls) * 1e3
         del vol_h
 
     # --- accuracy at the measured configuration, against the FP64 oracle
@@ -649,6 +770,7 @@ def main():
                 "value": world * upd_eff / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": proj.nbytes, "d2h_bytes_per_step": w.N ** 3 * 4,
                 "ms_per_step": ms_e2e, "steps": n_e2e,
+                "ms_per_call_min_median_max": [round(float(f(ms_calls)), 3) for f in (np.min, np.median, np.max)],
                 "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
                 "note": "host clock around whole calls; inside a call the upload (bands of detector rows) "
                         "overlaps the filter and the decomposition, the read-back (groups of slices) the "

@@ -115,8 +115,11 @@ constexpr int kConsumerWarps = 8;
 // adjacent detector rows per lane (the per-view bookkeeping -- table loads,
 // slot waits, decimated-view stores -- is shared by them): four with the
 // triangle's two running sums, two with the four of 2D-tap filters
-// (registers; measured: 2 -> 4 rows took 1.63 -> 1.48 ms at 512^3)
-__host__ __device__ constexpr int rows_per_lane(int H) { return H == 1 ? 4 : 2; }
+// (registers; measured: 2 -> 4 rows took 1.63 -> 1.48 ms at 512^3); half of
+// that where the launch would not fill two waves of the GPU (short row bands)
+__host__ __device__ constexpr int rows_per_lane(int H, bool wide = true) {
+    return (H == 1 ? 4 : 2) / (wide ? 1 : 2);
+}
 // ring shape per element type (measured): slots of kG views, kStages slots
 template <typename TQ>
 struct Ring {
@@ -228,7 +231,7 @@ __device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, floa
         row_cols<TQ, C, H>(a + rs * (uint32_t)r, f, w, acc[r], std::make_integer_sequence<int, C>{});
 }
 
-template <typename TQ, int C, int H>
+template <typename TQ, int C, int H, int RPL>
 __global__ void __launch_bounds__(kDecThreads)
 decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ Sp,
                      const int32_t *__restrict__ crop, const GeomEntry *__restrict__ geo,
@@ -237,7 +240,6 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     constexpr int ES = (int)sizeof(TQ);
     constexpr int kAlign = 16 / ES;
     constexpr int kG = Ring<TQ>::kG, kStages = Ring<TQ>::kStages;
-    constexpr int RPL = rows_per_lane(H);
     constexpr int VB = kConsumerWarps * RPL;   // rows per CTA (box height)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ring = smem_raw + ((128u - (tma::smem_u32(smem_raw) & 127u)) & 127u);
@@ -368,28 +370,43 @@ struct Rows {
     int layout, rowoff, rowend;
 };
 
-template <typename TQ, int C, int H>
+template <typename TQ, int C, int H, int RPL>
 cudaError_t launch_tma_shape(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st,
                              Rows rw, size_t smem, int tile_stride) {
-    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, H>>(smem);
+    cudaError_t e = ensure_smem<decompose_tma_kernel<TQ, C, H, RPL>>(smem);
     if (e != cudaSuccess) return e;
-    constexpr int VB = kConsumerWarps * rows_per_lane(H);
+    constexpr int VB = kConsumerWarps * RPL;
     dim3 grid(p.od.nsq, (rw.rowend - rw.rowoff + VB - 1) / VB);
-    decompose_tma_kernel<TQ, C, H><<<grid, kDecThreads, smem, st>>>(
+    decompose_tma_kernel<TQ, C, H, RPL><<<grid, kDecThreads, smem, st>>>(
         map, out, p.od.crop, p.od.geo, p.od.T, p.tapw, p.status, p.Tstride, p.g.P, p.D, p.Pd, rw.layout, Wc,
         tile_stride, rw.rowoff, rw.rowend);
     return cudaGetLastError();
 }
 
-template <typename TQ, int H>
-cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, Rows rw,
+template <typename TQ, int H, int RPL>
+cudaError_t launch_tma_c(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, Rows rw,
                          size_t smem, int tile_stride) {
     switch (dec_cols(p.Tstride)) {
-        case 1: return launch_tma_shape<TQ, 1, H>(p, map, out, Wc, st, rw, smem, tile_stride);
-        case 2: return launch_tma_shape<TQ, 2, H>(p, map, out, Wc, st, rw, smem, tile_stride);
-        case 4: return launch_tma_shape<TQ, 4, H>(p, map, out, Wc, st, rw, smem, tile_stride);
-        default: return launch_tma_shape<TQ, 8, H>(p, map, out, Wc, st, rw, smem, tile_stride);
+        case 1: return launch_tma_shape<TQ, 1, H, RPL>(p, map, out, Wc, st, rw, smem, tile_stride);
+        case 2: return launch_tma_shape<TQ, 2, H, RPL>(p, map, out, Wc, st, rw, smem, tile_stride);
+        case 4: return launch_tma_shape<TQ, 4, H, RPL>(p, map, out, Wc, st, rw, smem, tile_stride);
+        default: return launch_tma_shape<TQ, 8, H, RPL>(p, map, out, Wc, st, rw, smem, tile_stride);
     }
+}
+
+template <typename TQ, int H>
+cudaError_t launch_tma_h(const PlanImpl &p, const CUtensorMap &map, float *out, int Wc, cudaStream_t st, Rows rw,
+                         size_t smem, int tile_stride, bool wide) {
+    return wide ? launch_tma_c<TQ, H, rows_per_lane(H, true)>(p, map, out, Wc, st, rw, smem, tile_stride)
+                : launch_tma_c<TQ, H, rows_per_lane(H, false)>(p, map, out, Wc, st, rw, smem, tile_stride);
+}
+
+// the wide rows-per-lane shape unless its grid would not fill two waves
+bool wide_rows(const PlanImpl &p, int H, int nrows) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int vb = kConsumerWarps * rows_per_lane(H, true);
+    return (long long)p.od.nsq * ((nrows + vb - 1) / vb) >= 2LL * sms;
 }
 
 // TMA applies when Q's rows are whole 16-byte units, Q and S' are 16-byte
@@ -404,7 +421,8 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
     if ((p.g.Nu % kAlign) != 0 || ((uintptr_t)Q & 15) != 0 || ((uintptr_t)out & 15) != 0) return cudaSuccess;
     const int Wc = (p.od.Tmax + 1 + (kAlign - 1) + (kAlign - 1)) & ~(kAlign - 1);
     if (Wc > 256 || p.Tstride > 256 || p.D > kMaxTapD) return cudaSuccess;  // block offset: 8 bits of the code
-    const int VB = kConsumerWarps * rows_per_lane(p.tap_blocks);
+    const bool wide = wide_rows(p, p.tap_blocks, rw.rowend - rw.rowoff);
+    const int VB = kConsumerWarps * rows_per_lane(p.tap_blocks, wide);
     const int tile_stride = (VB * Wc + 63) & ~63;  // elements; 128-byte multiple for every type
     const int nstream = p.g.P + (2 * p.tap_blocks - 1) * p.D - 1;
     const size_t smem = 128 + sizeof(TQ) * (size_t)Ring<TQ>::kStages * Ring<TQ>::kG * tile_stride +
@@ -421,8 +439,8 @@ cudaError_t try_tma(const PlanImpl &p, const TQ *Q, float *out, cudaStream_t st,
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     if (encode_map_3d(&map, dt, Q, dims, strides, box) != cudaSuccess) return cudaSuccess;
     launched = true;
-    if (p.tap_blocks == 2) return launch_tma_h<TQ, 2>(p, map, out, Wc, st, rw, smem, tile_stride);
-    return launch_tma_h<TQ, 1>(p, map, out, Wc, st, rw, smem, tile_stride);
+    if (p.tap_blocks == 2) return launch_tma_h<TQ, 2>(p, map, out, Wc, st, rw, smem, tile_stride, wide);
+    return launch_tma_h<TQ, 1>(p, map, out, Wc, st, rw, smem, tile_stride, wide);
 }
 
 template <typename TQ>

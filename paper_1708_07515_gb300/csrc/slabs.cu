@@ -143,11 +143,14 @@ extern "C" int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_hos
 //     overlaps the next group's backprojection.
 namespace fdkod {
 
-// Four row bands: the strided copy of a band (one segment per view) keeps
-// near the contiguous copy rate down to about 256 KiB segments (measured:
-// 211 GB/s for two bands of 512^2 x 720 float32, 185 for four, 127 for eight).
-constexpr int kPipeChunks = 4;  // row bands of the upload
-constexpr int kPipeSlabs = 8;   // groups of slice pairs of the backprojection / read-back
+// Row bands of the upload, outside in: two thin outer bands of Nv/8 rows
+// (the outermost slice pairs read only those, so their backprojection can
+// start early), then bands of Nv/4 rows.  The strided copy of a band (one
+// segment per view) keeps near the contiguous copy rate down to about
+// 256 KiB segments (measured: 211 GB/s for two bands of 512^2 x 720
+// float32, 185 for four, 127 for eight).
+constexpr int kPipeChunks = 8;  // at most this many row bands
+constexpr int kPipeSlabs = 16;  // groups of slice pairs of the backprojection / read-back
 
 // The bands are filtered and decomposed on a stream of their own (in upload
 // order), and the groups' backprojections alternate between the caller's
@@ -261,14 +264,33 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
     // whole-detector launch does); an odd Nv, or a learned decimation (its
     // kernel takes every row at once), makes one band.
     const bool banded = (Nv % 2) == 0 && !p.net;
-    int rb = banded ? (Nv + kPipeChunks - 1) / kPipeChunks : Nv;
-    rb += rb & 1;
-    const int nbands = (Nv + rb - 1) / rb;
+    // band i covers rows bv[i] .. bv[i + 1] - 1 (even bounds); upload order:
+    // the two outer bands, then inwards, alternating bottom and top
+    int bv[kPipeChunks + 1], nbands = 0;
+    if (!banded) {
+        bv[0] = 0;
+        bv[1] = Nv;
+        nbands = 1;
+    } else {
+        const int outer = std::max(2, (Nv / 8) & ~1), inner = std::max(2, (Nv / 4) & ~1);
+        int lo = 0, hi = Nv, cuts_lo[kPipeChunks], cuts_hi[kPipeChunks], nl = 0, nh = 0;
+        for (int step = outer; lo < hi; step = inner) {  // walk inwards from both ends
+            if (nl + nh + 2 > kPipeChunks - 1 || hi - lo <= 2 * step) break;
+            lo += step;
+            hi -= step;
+            cuts_lo[nl++] = lo;
+            cuts_hi[nh++] = hi;
+        }
+        bv[nbands++] = 0;
+        for (int i = 0; i < nl; ++i) bv[nbands++] = cuts_lo[i];
+        for (int i = nh - 1; i >= 0; --i) bv[nbands++] = cuts_hi[i];
+        bv[nbands] = Nv;  // nbands = number of bands
+    }
     int order[kPipeChunks];  // outside in: 0, last, 1, last - 1, ...
     for (int i = 0, lo = 0, hi = nbands - 1; i < nbands; ++i) order[i] = (i & 1) ? hi-- : lo++;
     const size_t pitch = sizeof(float) * view;
     for (int i = 0; i < nbands; ++i) {
-        const int v0 = order[i] * rb, nb = std::min(rb, Nv - v0);
+        const int v0 = bv[order[i]], nb = bv[order[i] + 1] - v0;
         SLAB_TRY(cudaMemcpy2DAsync(hp.proj + (size_t)v0 * Nu, pitch, proj_host + (size_t)v0 * Nu, pitch,
                                    sizeof(float) * (size_t)nb * Nu, (size_t)P, cudaMemcpyHostToDevice, hp.up));
         SLAB_TRY(cudaEventRecord(hp.ev_up[order[i]], hp.up));
@@ -279,8 +301,8 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
     for (int i = 0; i < nbands; ++i) {
         const int bi = order[i];
         fdkod::Band rows;
-        rows.row0 = bi * rb;
-        rows.nrows = std::min(rb, Nv - rows.row0);
+        rows.row0 = bv[bi];
+        rows.nrows = bv[bi + 1] - bv[bi];
         rows.whole_arrays = true;
         cudaStream_t c = hp.comp2;
         SLAB_TRY(cudaStreamWaitEvent(c, hp.ev_up[bi], 0));
@@ -299,7 +321,7 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
         const int rc = fdkod_slab_rows(plan, z0, nz, &v0, &nr);
         if (rc != FDKOD_OK) return rc;
         for (int bi = 0; bi < nbands; ++bi)
-            if (bi * rb < v0 + nr && (bi + 1) * rb > v0) SLAB_TRY(cudaStreamWaitEvent(c, hp.ev_band[bi], 0));
+            if (bv[bi] < v0 + nr && bv[bi + 1] > v0) SLAB_TRY(cudaStreamWaitEvent(c, hp.ev_band[bi], 0));
         return FDKOD_OK;
     };
     const bool direct = p.D == 1;

@@ -224,6 +224,8 @@ WORKLOADS = {
     # small case of the 512 workload's square size (64) and D, for profiling
     "fdkod_256": Workload("fdkod_256^3_P360_s2_D4", 256, 360, 2, 4, 20, 0.01, 1500),
     "fdkod_512": Workload("fdkod_512^3_P720_s3_D4", 512, 720, 3, 4, 40, 0.01, 2000),
+    # the 512 workload's detector and squares with a quarter of its views, for profiling
+    "fdkod_512_p180": Workload("fdkod_512^3_P180_s3_D4", 512, 180, 3, 4, 40, 0.01, 2000),
     "fdkod_1024": Workload("fdkod_1024^3_P720_s4_D8", 1024, 720, 4, 8, 80, 0.0, 3000),
     "fdkod_2000": Workload("fdkod_2000^3_P720_s5_D16", 2000, 720, 5, 16, 150, 0.01, 5000),
 }
