@@ -771,6 +771,7 @@ def main():
                 "h2d_bytes_per_step": proj.nbytes, "d2h_bytes_per_step": w.N ** 3 * 4,
                 "ms_per_step": ms_e2e, "steps": n_e2e,
                 "ms_per_call_min_median_max": [round(float(f(ms_calls)), 3) for f in (np.min, np.median, np.max)],
+                "slowest_call": int(np.argmax(ms_calls)),
                 "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
                 "note": "host clock around whole calls; inside a call the upload (bands of detector rows) "
                         "overlaps the filter and the decomposition, the read-back (groups of slices) the "

@@ -335,8 +335,11 @@ int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, float *vol_hos
  *   overlap the compute; pageable memory works, with synchronous copies);
  * vol_host: host [N][N][N] float32, fully overwritten;
  * slab: slices per slab (>= 1, clamped to N);
- * device_bytes: if not NULL, receives the device memory the call allocated
- *   (all of it is freed before the call returns).
+ * device_bytes: if not NULL, receives the device memory of the slab
+ *   pipeline (band and slab buffers, filtered rows, decomposed data).  The
+ *   first call for a slab size allocates it; it stays with the plan for
+ *   later calls with the same slab size (another size replaces it) and is
+ *   freed by fdkod_destroy.  It is not counted in fdkod_plan_info.
  * Works with plans with or without the whole-volume workspace; the plan's
  * decimation taps and storage type apply.  Synchronous: returns once
  * vol_host holds the volume and the device status word has been read.

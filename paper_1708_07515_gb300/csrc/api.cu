@@ -60,6 +60,8 @@ void free_plan(PlanImpl &p) {
     cudaFree(p.status);
     free_host_pipe(p.pipe);
     p.pipe = nullptr;
+    free_slab_pipe(p.slabs);
+    p.slabs = nullptr;
 }
 
 double centre(int i, int n) { return (double)i - 0.5 * (double)(n - 1); }

@@ -737,14 +737,19 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
         return;
     }
 
-    // ---- consumers
+    // ---- consumers.  A voxel and its mirror go through the same operations
+    // on different samples, so they share packed two-lane FP32 instructions
+    // (x: lower slab, y: upper slab; each lane rounds as the scalar
+    // operation would): half the arithmetic instructions of two scalar
+    // updates.
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
     const int x = x0 + lx, y = y0 + ly;
     const bool active = x <= xe && y <= ye;
     const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
-    float lo[kZP], up[kZP];  // lower slab, upper (mirrored) slab
+    const float2 kM1 = make_float2(-1.f, -1.f);
+    float2 acc[kZP];  // (lower slab, upper mirrored slab)
 #pragma unroll
-    for (int i = 0; i < kZP; ++i) lo[i] = up[i] = 0.f;
+    for (int i = 0; i < kZP; ++i) acc[i] = make_float2(0.f, 0.f);
 
     for (int c = 0; c < nch; ++c) {
         const int sl = c % kPairSlots;
@@ -769,6 +774,7 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
             const float wgt = invU * invU;
             const float a1 = wgt * (t - tf);
             const float a0 = wgt - a1;
+            const float2 A1 = make_float2(a1, a1), A0 = make_float2(a0, a0);
             // window row of slice p0 (lower slab), in 9.23 fixed point
             const float vb0 = fmaf(invU, -0.5f * (float)(kZP - 1) - s_zcr[sl][w] * dd, pb.w);
             uint32_t V = __float2uint_rn(vb0 * kFix);
@@ -777,17 +783,28 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
             const uint32_t bL = sbase + (uint32_t)ES * (win(sl, w, 0) + (uint32_t)(int)tf);
             const uint32_t bU = sbase + (uint32_t)ES * (win(sl, w, 1) + (uint32_t)(int)tf);
             const uint32_t KLU = (uint32_t)(s_C[sl][w] - 1) * ROWB + bU + bL;
+            // column-interpolated samples (U^-2 weighted) of the pair's first
+            // row (lower row r, upper row C - r) and of its second row
+            auto first = [&](uint32_t aL, uint32_t aU) {
+                return __ffma2_rn(A1, make_float2(Lds<TS, ES>::f(aL), Lds<TS, ROWB + ES>::f(aU)),
+                                  __fmul2_rn(A0, make_float2(Lds<TS, 0>::f(aL), Lds<TS, ROWB>::f(aU))));
+            };
+            auto second = [&](uint32_t aL, uint32_t aU) {
+                return __ffma2_rn(A1, make_float2(Lds<TS, ROWB + ES>::f(aL), Lds<TS, ES>::f(aU)),
+                                  __fmul2_rn(A0, make_float2(Lds<TS, ROWB>::f(aL), Lds<TS, 0>::f(aU))));
+            };
+            // row fraction (both lanes) from the fixed-point row coordinate
+            auto frac = [&](uint32_t Vc) {
+                const float fb = __uint_as_float((Vc & 0x7fffffu) | 0x3f800000u);
+                return __fadd2_rn(make_float2(fb, fb), kM1);
+            };
             if (stepA) {
                 // 1/U <= 1: the row advances by 0 or 1 per slice
                 uint32_t r = V >> 23;
                 uint32_t aL = r * ROWB + bL, aU = KLU - aL;
-                float f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
-                float lA = fmaf(a1, Lds<TS, ES>::f(aL), a0 * Lds<TS, 0>::f(aL));
-                float lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
-                float uA = fmaf(a1, Lds<TS, ROWB + ES>::f(aU), a0 * Lds<TS, ROWB>::f(aU));
-                float uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
-                lo[0] = fmaf(f, lB - lA, lo[0] + lA);
-                up[0] = fmaf(f, uB - uA, up[0] + uA);
+                float2 A = first(aL, aU);
+                float2 B = second(aL, aU);
+                acc[0] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[0], A));
 #pragma unroll
                 for (int i = 1; i < kZP; ++i) {
                     V += dV;
@@ -796,26 +813,18 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
                     r = rn;
                     aL = r * ROWB + bL;
                     aU = KLU - aL;
-                    f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
-                    lA = adv ? lB : lA;
-                    uA = adv ? uB : uA;
-                    lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
-                    uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
-                    lo[i] = fmaf(f, lB - lA, lo[i] + lA);
-                    up[i] = fmaf(f, uB - uA, up[i] + uA);
+                    A = adv ? B : A;
+                    B = second(aL, aU);
+                    acc[i] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[i], A));
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < kZP; ++i) {
                     const uint32_t r = V >> 23;
                     const uint32_t aL = r * ROWB + bL, aU = KLU - aL;
-                    const float f = __uint_as_float((V & 0x7fffffu) | 0x3f800000u) - 1.0f;
-                    const float lA = fmaf(a1, Lds<TS, ES>::f(aL), a0 * Lds<TS, 0>::f(aL));
-                    const float lB = fmaf(a1, Lds<TS, ROWB + ES>::f(aL), a0 * Lds<TS, ROWB>::f(aL));
-                    const float uA = fmaf(a1, Lds<TS, ROWB + ES>::f(aU), a0 * Lds<TS, ROWB>::f(aU));
-                    const float uB = fmaf(a1, Lds<TS, ES>::f(aU), a0 * Lds<TS, 0>::f(aU));
-                    lo[i] = fmaf(f, lB - lA, lo[i] + lA);
-                    up[i] = fmaf(f, uB - uA, up[i] + uA);
+                    const float2 A = first(aL, aU);
+                    const float2 B = second(aL, aU);
+                    acc[i] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[i], A));
                     V += dV;
                 }
             }
@@ -829,8 +838,8 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
             const int pz = p0 + i;
             if (pz < a.pend) {
                 const int zu = a.N - 1 - pz;
-                a.vol[((size_t)pz * a.N + y) * a.N + x] = lo[i] * a.scale;
-                if (zu != pz) a.vol[((size_t)zu * a.N + y) * a.N + x] = up[i] * a.scale;
+                a.vol[((size_t)pz * a.N + y) * a.N + x] = acc[i].x * a.scale;
+                if (zu != pz) a.vol[((size_t)zu * a.N + y) * a.N + x] = acc[i].y * a.scale;
             }
         }
     }

@@ -205,30 +205,71 @@ struct Ld1<__half, OFF> {
 // Columns past T are computed too (no branch; their sums are never stored):
 // their loads stay inside the CTA's shared memory, within the next row, the
 // next slot or the ring's tail slack of kColSlack(C) bytes.
+//
+// Rows are taken in pairs (r, r + 1) where the lane has an even number of
+// them: the two rows share the shift fraction and the tap weights, so one
+// packed two-lane FP32 instruction (each lane rounded as the scalar
+// operation would be) does the work of two.  acc[rp][m][i] holds running
+// sum m of column i for rows 2 rp (x) and 2 rp + 1 (y); a lane with one row
+// uses x only.
 template <typename TQ, int I, int C, int H>
-__device__ __forceinline__ void col_step(uint32_t ar, float f, float4 w, float (&acc)[2 * H][C]) {
+__device__ __forceinline__ void col_step(uint32_t ar, float f, float4 w, float2 (&acc)[2 * H][C]) {
     constexpr int ES = (int)sizeof(TQ);
     const float a0 = Ld1<TQ, ES * 32 * I>::f(ar), a1 = Ld1<TQ, ES * (32 * I + 1)>::f(ar);
     const float smp = fmaf(f, a1 - a0, a0);
-    acc[0][I] = fmaf(w.x, smp, acc[0][I]);
-    acc[1][I] = fmaf(w.y, smp, acc[1][I]);
+    acc[0][I].x = fmaf(w.x, smp, acc[0][I].x);
+    acc[1][I].x = fmaf(w.y, smp, acc[1][I].x);
     if (H == 2) {
-        acc[2][I] = fmaf(w.z, smp, acc[2][I]);
-        acc[3][I] = fmaf(w.w, smp, acc[3][I]);
+        acc[2][I].x = fmaf(w.z, smp, acc[2][I].x);
+        acc[3][I].x = fmaf(w.w, smp, acc[3][I].x);
     }
 }
 
+template <typename TQ, int I, int C, int H>
+__device__ __forceinline__ void col_step2(uint32_t ar, uint32_t ar2, float2 f2, const float2 (&w2)[2 * H],
+                                          float2 (&acc)[2 * H][C]) {
+    constexpr int ES = (int)sizeof(TQ);
+    const float2 a0 = make_float2(Ld1<TQ, ES * 32 * I>::f(ar), Ld1<TQ, ES * 32 * I>::f(ar2));
+    const float2 a1 = make_float2(Ld1<TQ, ES * (32 * I + 1)>::f(ar), Ld1<TQ, ES * (32 * I + 1)>::f(ar2));
+    // a0 + f (a1 - a0), the difference as a1 + (-1) a0 (one rounding)
+    const float2 smp = __ffma2_rn(f2, __ffma2_rn(a0, make_float2(-1.f, -1.f), a1), a0);
+#pragma unroll
+    for (int m = 0; m < 2 * H; ++m) acc[m][I] = __ffma2_rn(w2[m], smp, acc[m][I]);
+}
+
 template <typename TQ, int C, int H, int... I>
-__device__ __forceinline__ void row_cols(uint32_t ar, float f, float4 w, float (&acc)[2 * H][C],
+__device__ __forceinline__ void row_cols(uint32_t ar, float f, float4 w, float2 (&acc)[2 * H][C],
                                          std::integer_sequence<int, I...>) {
     (col_step<TQ, I, C, H>(ar, f, w, acc), ...);
 }
 
+template <typename TQ, int C, int H, int... I>
+__device__ __forceinline__ void row_pair_cols(uint32_t ar, uint32_t ar2, float2 f2, const float2 (&w2)[2 * H],
+                                              float2 (&acc)[2 * H][C], std::integer_sequence<int, I...>) {
+    (col_step2<TQ, I, C, H>(ar, ar2, f2, w2, acc), ...);
+}
+
 template <typename TQ, int C, int H, int RPL>
-__device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, float4 w, float (&acc)[RPL][2 * H][C]) {
+__device__ __forceinline__ void view_cols(uint32_t a, uint32_t rs, float f, float4 w,
+                                          float2 (&acc)[(RPL + 1) / 2][2 * H][C]) {
+    if constexpr (RPL % 2 == 0) {
+        const float2 f2 = make_float2(f, f);
+        float2 w2[2 * H];
+        w2[0] = make_float2(w.x, w.x);
+        w2[1] = make_float2(w.y, w.y);
+        if constexpr (H == 2) {
+            w2[2] = make_float2(w.z, w.z);
+            w2[3] = make_float2(w.w, w.w);
+        }
 #pragma unroll
-    for (int r = 0; r < RPL; ++r)
-        row_cols<TQ, C, H>(a + rs * (uint32_t)r, f, w, acc[r], std::make_integer_sequence<int, C>{});
+        for (int rp = 0; rp < RPL / 2; ++rp) {
+            const uint32_t ar = a + rs * (uint32_t)(2 * rp);
+            row_pair_cols<TQ, C, H>(ar, ar + rs, f2, w2, acc[rp], std::make_integer_sequence<int, C>{});
+        }
+    } else {
+        static_assert(RPL == 1, "an odd number of rows per lane is one row");
+        row_cols<TQ, C, H>(a, f, w, acc[0], std::make_integer_sequence<int, C>{});
+    }
 }
 
 template <typename TQ, int C, int H, int RPL>
@@ -298,13 +339,14 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
     const int rib = ty * RPL;  // first of the warp's rows in the band
     const int v = v0 + rib;
     const int T = Tq[q];
-    float acc[RPL][2 * H][C];
+    constexpr int RP = (RPL + 1) / 2;  // row pairs
+    float2 acc[RP][2 * H][C];
 #pragma unroll
-    for (int r = 0; r < RPL; ++r)
+    for (int r = 0; r < RP; ++r)
 #pragma unroll
         for (int m = 0; m < 2 * H; ++m)
 #pragma unroll
-            for (int i = 0; i < C; ++i) acc[r][m][i] = 0.f;
+            for (int i = 0; i < C; ++i) acc[r][m][i] = make_float2(0.f, 0.f);
     const size_t vstride = (size_t)Nv * Tstride;
     float *out = Sp + ((size_t)q * Pd * Nv + v) * Tstride + tx;  // row v; row v + r is r Tstride further
     const uint32_t lane_addr = tma::smem_u32(ring) + (uint32_t)(ES * (rib * Wc + tx));
@@ -336,18 +378,20 @@ decompose_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict
                             if (v + r < rowend) {
                                 float *dst = out + (size_t)jst * vstride + (size_t)r * Tstride;
 #pragma unroll
-                                for (int i = 0; i < C; ++i)
-                                    if (tx + 32 * i < Tstride) dst[32 * i] = tx + 32 * i < T ? acc[r][0][i] : 0.f;
+                                for (int i = 0; i < C; ++i) {
+                                    const float val = (r & 1) ? acc[r / 2][0][i].y : acc[r / 2][0][i].x;
+                                    if (tx + 32 * i < Tstride) dst[32 * i] = tx + 32 * i < T ? val : 0.f;
+                                }
                             }
                         }
                     }
 #pragma unroll
-                    for (int r = 0; r < RPL; ++r)
+                    for (int r = 0; r < RP; ++r)
 #pragma unroll
                         for (int i = 0; i < C; ++i) {
 #pragma unroll
                             for (int m = 0; m < 2 * H - 1; ++m) acc[r][m][i] = acc[r][m + 1][i];
-                            acc[r][2 * H - 1][i] = 0.f;
+                            acc[r][2 * H - 1][i] = make_float2(0.f, 0.f);
                         }
                 }
             }

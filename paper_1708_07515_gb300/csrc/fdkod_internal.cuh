@@ -70,6 +70,10 @@ struct __align__(16) NetWeights {
 // Device side of the whole-volume host-buffer pipeline (slabs.cu).
 struct HostPipe;
 void free_host_pipe(HostPipe *hp);
+// Buffers, streams and events of the slab-wise pipeline (slabs.cu), kept
+// from one fdkod_reconstruct_slabs call to the next with the same slab size.
+struct SlabPipe;
+void free_slab_pipe(SlabPipe *sp);
 
 struct PlanImpl {
     fdkod_geometry g{};
@@ -106,6 +110,7 @@ struct PlanImpl {
     int64_t wait_ns = 0;       // bounded-wait limit, 0 = the kernels' default
     // device buffers and streams of fdkod_reconstruct (made on its first call)
     HostPipe *pipe = nullptr;
+    SlabPipe *slabs = nullptr;
 };
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more

@@ -34,18 +34,24 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sum and difference as packed two-lane FP32 instructions (real and
+// imaginary part in one instruction, each rounded as the scalar operation
+// would be; the difference is a + (-1) b with one rounding).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 // multiply by -i
 __device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
+// a - i d and a + i d (scalar: the swapped operand would cost a move)
+__device__ __forceinline__ float2 cadd_mi(float2 a, float2 d) { return make_float2(a.x + d.y, a.y - d.x); }
+__device__ __forceinline__ float2 csub_mi(float2 a, float2 d) { return make_float2(a.x - d.y, a.y + d.x); }
 
 // 4-point forward DFT in place: (a, b, c, d) -> (X0, X1, X2, X3)
 __device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
     const float2 s02 = cadd(a, c), d02 = csub(a, c), s13 = cadd(b, d), d13 = csub(b, d);
     a = cadd(s02, s13);
     c = csub(s02, s13);
-    b = cadd(d02, cmi(d13));
-    d = csub(d02, cmi(d13));
+    b = cadd_mi(d02, d13);
+    d = csub_mi(d02, d13);
 }
 
 constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
@@ -253,6 +259,11 @@ __device__ __forceinline__ void fft(float2 *buf, const float2 *tw, int lgL, int 
 struct RowMap {
     int rows_per_view, view_rows, off;
     __device__ __forceinline__ long long mem(long long r) const {
+        if (view_rows == rows_per_view) return r + off;  // the arrays hold just these rows
+        if (r <= 0x7fffffffLL) {                          // 32-bit division where it suffices
+            const unsigned k = (unsigned)r / (unsigned)rows_per_view;
+            return (long long)k * view_rows + off + ((unsigned)r - k * (unsigned)rows_per_view);
+        }
         const long long k = r / rows_per_view;
         return k * view_rows + off + (r - k * rows_per_view);
     }
@@ -278,20 +289,23 @@ filter_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const float *_
     const float bA = (float)(row0 + (int)(rowA % rows_per_view)) - 0.5f * (float)(Nv - 1);
     const float bB = (float)(row0 + (int)(rowB % rows_per_view)) - 0.5f * (float)(Nv - 1);
     const float R2 = R * R;
+    // memory rows, once per thread (a 64-bit division)
+    const long long mA = hasA ? rm.mem(rowA) : 0, mB = hasB ? rm.mem(rowB) : 0;
+    const float *pa = proj + mA * Nu, *pb = proj + mB * Nu;
     for (int i = lt; i < L / 2; i += nt) {  // the upper half is never read (see pass)
         float2 v = make_float2(0.f, 0.f);
         if (i < Nu) {
             const float u = (float)i - 0.5f * (float)(Nu - 1);
-            if (hasA) v.x = __ldg(proj + rm.mem(rowA) * Nu + i) * (R * rsqrtf(R2 + u * u + bA * bA));
-            if (hasB) v.y = __ldg(proj + rm.mem(rowB) * Nu + i) * (R * rsqrtf(R2 + u * u + bB * bB));
+            if (hasA) v.x = __ldg(pa + i) * (R * rsqrtf(R2 + u * u + bA * bA));
+            if (hasB) v.y = __ldg(pb + i) * (R * rsqrtf(R2 + u * u + bB * bB));
         }
         buf[pad(i)] = v;
     }
     __syncthreads();
     Sink<TQ> sink;
     sink.H = H;
-    sink.qa = hasA ? Q + rm.mem(rowA) * Nu : nullptr;
-    sink.qb = hasB ? Q + rm.mem(rowB) * Nu : nullptr;
+    sink.qa = hasA ? Q + mA * Nu : nullptr;
+    sink.qb = hasB ? Q + mB * Nu : nullptr;
     sink.Nu = Nu;
     fft<kToSpectrum>(buf, tw, lgL, lt, nt, sink);
     fft<kToQ>(buf, tw, lgL, lt, nt, sink);

@@ -15,24 +15,20 @@
 
 #include "fdkod_internal.cuh"
 
-namespace {
+namespace fdkod {
 
-using fdkod::Band;
-using fdkod::PlanImpl;
-
-struct Resources {
+// Two band buffers and two slab buffers (double-buffered), the filtered
+// rows and the decomposed data of one slab, the upload and read-back
+// streams and the per-slab events, made on the first call for a slab size
+// and kept with the plan (a call that allocated tens of GB each time spent
+// much of its time in cudaMalloc and cudaFree).
+struct SlabPipe {
+    int slab = 0, nsl = 0;
     std::vector<void *> mem;
     std::vector<cudaEvent_t> ev;
+    void *proj_b[2] = {}, *vol_b[2] = {}, *Q = nullptr, *S = nullptr;
     cudaStream_t up = nullptr, down = nullptr;
     int64_t bytes = 0;
-    ~Resources() {
-        if (up) cudaStreamSynchronize(up);
-        if (down) cudaStreamSynchronize(down);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (up) cudaStreamDestroy(up);
-        if (down) cudaStreamDestroy(down);
-        for (void *p : mem) cudaFree(p);
-    }
     cudaError_t alloc(void **p, size_t n) {
         cudaError_t e = cudaMalloc(p, std::max<size_t>(n, 1));
         if (e == cudaSuccess) {
@@ -42,6 +38,25 @@ struct Resources {
         return e;
     }
 };
+
+void free_slab_pipe(SlabPipe *sp) {
+    if (!sp) return;
+    if (sp->up) cudaStreamSynchronize(sp->up);
+    if (sp->down) cudaStreamSynchronize(sp->down);
+    for (cudaEvent_t e : sp->ev)
+        if (e) cudaEventDestroy(e);
+    if (sp->up) cudaStreamDestroy(sp->up);
+    if (sp->down) cudaStreamDestroy(sp->down);
+    for (void *p : sp->mem) cudaFree(p);
+    delete sp;
+}
+
+}  // namespace fdkod
+
+namespace {
+
+using fdkod::Band;
+using fdkod::PlanImpl;
 
 int status_of(cudaError_t e) {
     if (e == cudaSuccess) return FDKOD_OK;
@@ -53,6 +68,39 @@ int status_of(cudaError_t e) {
         const int _rc = status_of(expr);       \
         if (_rc != FDKOD_OK) return _rc;       \
     } while (0)
+
+cudaError_t make_slab_pipe(const PlanImpl &p, int slab, int nsl, int max_rows, fdkod::SlabPipe **out) {
+    using fdkod::SlabPipe;
+    SlabPipe *sp = new (std::nothrow) SlabPipe;
+    if (!sp) return cudaErrorMemoryAllocation;
+    const int N = p.g.N, Nu = p.g.Nu, P = p.g.P;
+    const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
+    const size_t band = (size_t)P * max_rows * Nu;  // samples of one band of rows
+    const size_t vslab = (size_t)slab * N * N;      // voxels of one slab
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = sp->alloc(&sp->proj_b[b], sizeof(float) * band);
+        if (e == cudaSuccess) e = sp->alloc(&sp->vol_b[b], sizeof(float) * vslab);
+    }
+    if (e == cudaSuccess) e = sp->alloc(&sp->Q, es * band);
+    if (e == cudaSuccess && p.D > 1)
+        e = sp->alloc(&sp->S, sizeof(float) * (size_t)p.od.nsq * p.Pd * max_rows * p.Tstride);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sp->up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sp->down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        sp->ev.assign(4 * (size_t)nsl, nullptr);
+        for (auto &ev : sp->ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        fdkod::free_slab_pipe(sp);
+        return e;
+    }
+    sp->slab = slab;
+    sp->nsl = nsl;
+    *out = sp;
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -72,25 +120,25 @@ extern "C" int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_hos
         if (rc != FDKOD_OK) return rc;
         max_rows = std::max(max_rows, (int)nr[i]);
     }
-    const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
-    const size_t band = (size_t)P * max_rows * Nu;  // samples of one band of rows
-    const size_t vslab = (size_t)slab * N * N;      // voxels of one slab
-
-    Resources r;
-    void *proj_b[2], *vol_b[2], *Q = nullptr, *S = nullptr;
-    for (int b = 0; b < 2; ++b) {
-        SLAB_TRY(r.alloc(&proj_b[b], sizeof(float) * band));
-        SLAB_TRY(r.alloc(&vol_b[b], sizeof(float) * vslab));
+    if (p.slabs && p.slabs->slab != slab) {  // another slab size: new buffers
+        fdkod::free_slab_pipe(p.slabs);
+        p.slabs = nullptr;
     }
-    SLAB_TRY(r.alloc(&Q, es * band));
-    if (p.D > 1) SLAB_TRY(r.alloc(&S, sizeof(float) * (size_t)p.od.nsq * p.Pd * max_rows * p.Tstride));
+    if (!p.slabs) {
+        fdkod::SlabPipe *sp = nullptr;
+        SLAB_TRY(make_slab_pipe(p, slab, nsl, max_rows, &sp));
+        p.slabs = sp;
+    }
+    fdkod::SlabPipe &r = *p.slabs;
     if (device_bytes) *device_bytes = r.bytes;
-    SLAB_TRY(cudaStreamCreateWithFlags(&r.up, cudaStreamNonBlocking));
-    SLAB_TRY(cudaStreamCreateWithFlags(&r.down, cudaStreamNonBlocking));
-    r.ev.assign(4 * (size_t)nsl, nullptr);
-    for (auto &e : r.ev) SLAB_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    void **proj_b = r.proj_b, **vol_b = r.vol_b, *Q = r.Q, *S = r.S;
     cudaEvent_t *ev_up = r.ev.data(), *ev_filt = ev_up + nsl, *ev_comp = ev_filt + nsl, *ev_down = ev_comp + nsl;
     cudaStream_t comp = (cudaStream_t)stream;
+    // the previous call's read-backs and the caller's earlier work come first
+    SLAB_TRY(cudaEventRecord(ev_comp[0], comp));
+    SLAB_TRY(cudaStreamWaitEvent(r.up, ev_comp[0], 0));
+    SLAB_TRY(cudaEventRecord(ev_down[0], r.down));
+    SLAB_TRY(cudaStreamWaitEvent(comp, ev_down[0], 0));
 
     for (int i = 0; i < nsl; ++i) {
         const int b = i & 1;
@@ -126,6 +174,7 @@ extern "C" int fdkod_reconstruct_slabs(fdkod_plan_t *plan, const float *proj_hos
         SLAB_TRY(cudaEventRecord(ev_down[i], r.down));
     }
     SLAB_TRY(cudaStreamSynchronize(r.down));
+    SLAB_TRY(cudaStreamSynchronize(r.up));
     SLAB_TRY(cudaStreamSynchronize(comp));
     return fdkod_last_device_status(plan, stream);
 }
