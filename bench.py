@@ -772,6 +772,7 @@ def main():
                 "ms_per_step": ms_e2e, "steps": n_e2e,
                 "ms_per_call_min_median_max": [round(float(f(ms_calls)), 3) for f in (np.min, np.median, np.max)],
                 "slowest_call": int(np.argmax(ms_calls)),
+                "value_at_median_call": world * upd_eff / (float(np.median(ms_calls)) * 1e-3),
                 "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
                 "note": "host clock around whole calls; inside a call the upload (bands of detector rows) "
                         "overlaps the filter and the decomposition, the read-back (groups of slices) the "

@@ -746,7 +746,6 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
     const int x = x0 + lx, y = y0 + ly;
     const bool active = x <= xe && y <= ye;
     const float dx = (float)x - half_n - xc, dy = (float)y - half_n - yc;
-    const float2 kM1 = make_float2(-1.f, -1.f);
     float2 acc[kZP];  // (lower slab, upper mirrored slab)
 #pragma unroll
     for (int i = 0; i < kZP; ++i) acc[i] = make_float2(0.f, 0.f);
@@ -793,10 +792,12 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
                 return __ffma2_rn(A1, make_float2(Lds<TS, ROWB + ES>::f(aL), Lds<TS, ES>::f(aU)),
                                   __fmul2_rn(A0, make_float2(Lds<TS, ROWB>::f(aL), Lds<TS, 0>::f(aU))));
             };
-            // row fraction (both lanes) from the fixed-point row coordinate
-            auto frac = [&](uint32_t Vc) {
+            // row weights 1 - f and f (both lanes) from the fixed-point row
+            // coordinate: fb = 1 + f exactly, so 2 - fb and fb - 1 are exact
+            auto rowlerp = [&](uint32_t Vc, float2 A, float2 B, float2 acc_i) {
                 const float fb = __uint_as_float((Vc & 0x7fffffu) | 0x3f800000u);
-                return __fadd2_rn(make_float2(fb, fb), kM1);
+                const float f = fb - 1.0f, g = 2.0f - fb;
+                return __ffma2_rn(make_float2(f, f), B, __ffma2_rn(make_float2(g, g), A, acc_i));
             };
             if (stepA) {
                 // 1/U <= 1: the row advances by 0 or 1 per slice
@@ -804,7 +805,7 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
                 uint32_t aL = r * ROWB + bL, aU = KLU - aL;
                 float2 A = first(aL, aU);
                 float2 B = second(aL, aU);
-                acc[0] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[0], A));
+                acc[0] = rowlerp(V, A, B, acc[0]);
 #pragma unroll
                 for (int i = 1; i < kZP; ++i) {
                     V += dV;
@@ -815,7 +816,7 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
                     aU = KLU - aL;
                     A = adv ? B : A;
                     B = second(aL, aU);
-                    acc[i] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[i], A));
+                    acc[i] = rowlerp(V, A, B, acc[i]);
                 }
             } else {
 #pragma unroll
@@ -824,7 +825,7 @@ bp_pair_kernel(const __grid_constant__ CUtensorMap tmap, BpPairParams a) {
                     const uint32_t aL = r * ROWB + bL, aU = KLU - aL;
                     const float2 A = first(aL, aU);
                     const float2 B = second(aL, aU);
-                    acc[i] = __ffma2_rn(frac(V), __ffma2_rn(A, kM1, B), __fadd2_rn(acc[i], A));
+                    acc[i] = rowlerp(V, A, B, acc[i]);
                     V += dV;
                 }
             }

@@ -18,6 +18,7 @@
 #include <utility>
 
 #include "fdkod_internal.cuh"
+#include "packed.cuh"
 #include "tma.cuh"
 
 namespace fdkod {
@@ -231,8 +232,8 @@ __device__ __forceinline__ void col_step2(uint32_t ar, uint32_t ar2, float2 f2, 
     constexpr int ES = (int)sizeof(TQ);
     const float2 a0 = make_float2(Ld1<TQ, ES * 32 * I>::f(ar), Ld1<TQ, ES * 32 * I>::f(ar2));
     const float2 a1 = make_float2(Ld1<TQ, ES * (32 * I + 1)>::f(ar), Ld1<TQ, ES * (32 * I + 1)>::f(ar2));
-    // a0 + f (a1 - a0), the difference as a1 + (-1) a0 (one rounding)
-    const float2 smp = __ffma2_rn(f2, __ffma2_rn(a0, make_float2(-1.f, -1.f), a1), a0);
+    // a0 + f (a1 - a0)
+    const float2 smp = __ffma2_rn(f2, fsub2(a1, a0), a0);
 #pragma unroll
     for (int m = 0; m < 2 * H; ++m) acc[m][I] = __ffma2_rn(w2[m], smp, acc[m][I]);
 }

@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "fdkod_internal.cuh"
+#include "packed.cuh"
 #include "tma.cuh"
 
 namespace fdkod {
@@ -36,9 +37,9 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 // Complex sum and difference as packed two-lane FP32 instructions (real and
 // imaginary part in one instruction, each rounded as the scalar operation
-// would be; the difference is a + (-1) b with one rounding).
+// would be).
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return fsub2(a, b); }
 // multiply by -i
 __device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
 // a - i d and a + i d (scalar: the swapped operand would cost a move)
