@@ -271,17 +271,22 @@ def stage_rooflines(w, info, stages, qtype, peaks):
 
 
 def net_weights(path, D, seed=11):
-    """(weights, source) of the learned decimation for --taps net."""
+    """(weights, source, base taps or None) of the learned decimation for
+    --taps net; the base taps (the plain low-pass under the net) sit beside
+    the weights as <name>_taps.npy when the net was trained on top of
+    learned linear taps, else the base is the triangle."""
     if path is None:
         cand = os.path.join(ROOT, "paper_1708_07515_gb300", "net_weights", f"D{D}.npy")
         if os.path.exists(cand):
             path = cand
     if path is not None:
-        return np.load(path).astype(np.float32), os.path.relpath(path, ROOT)
+        tp = path[:-4] + "_taps.npy" if path.endswith(".npy") else path + "_taps.npy"
+        base = np.load(tp).astype(np.float64) if os.path.exists(tp) else None
+        return np.load(path).astype(np.float32), os.path.relpath(path, ROOT), base
     rng = np.random.default_rng(seed)
     w = np.concatenate([rng.standard_normal(80) * 0.4, rng.standard_normal(1280) * 0.15,
                         rng.standard_normal(80) * 0.01]).astype(np.float32)
-    return w, f"seeded random weights (seed {seed}; throughput does not depend on the values)"
+    return w, f"seeded random weights (seed {seed}; throughput does not depend on the values)", None
 
 
 def net_roofline(w, info, T, stages, peaks):
@@ -591,10 +596,10 @@ def main():
         zs_fit = np.linspace(w.N // 8, w.N - 1 - w.N // 8, 16).round().astype(int)
         taps = learn.learn(w.R, w.N, w.P, w.s, w.D, 2, train, zs_fit)
         del train
-    net_w = net_src = None
+    net_w = net_src = net_base = None
     if args.taps == "net":
-        net_w, net_src = net_weights(args.net_weights, w.D)
-        taps = "triangle"
+        net_w, net_src, net_base = net_weights(args.net_weights, w.D)
+        taps = "triangle" if net_base is None else net_base
     plan = fd.Plan(w.R, w.N, w.Nu, w.Nv, w.P, w.s, w.D, qtype=args.qtype, taps=taps)
     if net_w is not None:
         plan.set_net(net_w)
@@ -711,7 +716,7 @@ def main():
             nsq = 4 ** w.s
             squares = None if nsq <= 64 else sorted(np.random.default_rng(w.seed).choice(nsq, 16, replace=False))
             ref_od = oracle.fdkod_net_slices(Qo, w.R, w.N, w.s, w.D, plan.net, zs, act_round="bf16",
-                                             squares=squares)
+                                             squares=squares, taps=None if net_base is None else plan.taps)
         else:
             squares = None
             ref_od = oracle.fdkod_slices(Qo, w.R, w.N, w.s, w.D, zs,
@@ -793,7 +798,8 @@ def main():
             "roofline_smem": {"achieved": smem_ach, "peak": smem_peak, "unit": "GB/s", "frac": smem_ach / smem_peak,
                               "bytes_per_update": SMEM_BYTES_PER_UPDATE},
             "roofline_stages": stage_rooflines(w, info, stages, args.qtype, peaks),
-            **({"roofline_net": net_roofline(w, info, plan.bounds()["T"], stages, peaks), "net_weights": net_src}
+            **({"roofline_net": net_roofline(w, info, plan.bounds()["T"], stages, peaks), "net_weights": net_src,
+                 "net_base": "triangle" if net_base is None else "learned linear taps (support 2D)"}
                if net_w is not None else {}),
             "stages_ms": stages,
             "plain_fdk": {"value": world * upd_eff / (ms_plain * 1e-3), "ms_per_step": ms_plain,

@@ -18,7 +18,10 @@ slices:
   5. Adam on the 1440 master weights (host).
 
 The loss is sum e^2 / sum f_FDK^2 over the step's slices.  Layer 3 starts
-at zero, so training starts from the plain low-pass.
+at zero, so training starts from the plain low-pass.  The plain low-pass is
+the triangle, or (--base learned) the linear taps of support 2D fitted to
+full FDK on the same training scans (learn.py): the net then learns a
+residual on top of the best linear filter, and starts exactly at it.
 
     python -m paper_1708_07515_gb300.learn_net --N 512 --P 720 --s 3 --D 4
 
@@ -254,6 +257,9 @@ def main(argv=None):
     ap.add_argument("--init", choices=["linear", "random"], default="linear",
                     help="start at the best linear FIR within the net's reach (13 taps) or at random layers 1-2 "
                          "with a zero layer 3")
+    ap.add_argument("--base", choices=["triangle", "learned"], default="triangle",
+                    help="plain low-pass under the net: the triangle, or the learned linear taps of support 2D "
+                         "(fitted on the training scans; written beside --out as <out>_taps.npy)")
     args = ap.parse_args(argv)
     N, P, s, D = args.N, args.P, args.s, args.D
     R = 4.0 * N
@@ -263,17 +269,24 @@ def main(argv=None):
         return phantom.project_gpu(phantom.make_phantom(seed, N, args.ellipsoids), R, N, N, P)
 
     zs = np.linspace(N // 8, N - 1 - N // 8, args.eval_slices).round().astype(int)
-    tr = Trainer(R, N, P, s, D)
+    projs = [scan(8000 + i) for i in range(args.train)]
+    base = None
+    if args.base == "learned":
+        # the best linear taps of support 2D: the net's residual starts there
+        from . import learn
+        base = learn.learn(R, N, P, s, D, 2, projs, zs)
+    tr = Trainer(R, N, P, s, D, taps="triangle" if base is None else base)
     try:
-        projs = [scan(8000 + i) for i in range(args.train)]
         for p in projs:
             tr.add_scan(p)
         t0 = time.time()
         w0 = None
         if args.init == "linear":
-            g = linear_fit(R, N, P, s, D, projs, zs)
+            # the 13-tap linear correction of the base within the net's reach
+            # (zero on top of the learned taps, which are already the
+            # optimum of a wider support)
+            g = linear_fit(R, N, P, s, D, projs, zs) if base is None else {}
             w0 = linear_config(g, args.seed)
-            init_err = tr.rel_rmse(w0, tr.scans, zs[::4])
         w, curve = train(tr, args.steps, args.lr, args.slices, args.seed, w0=w0, log_every=args.log_every,
                          val_slices=zs[::4])
         t_train = time.time() - t0
@@ -281,12 +294,16 @@ def main(argv=None):
         for i in range(args.test):
             tr.add_scan(scan(9000 + i))
             held.append(tr.scans.pop())
-        errs = {"triangle": tr.rel_rmse(None, held, zs), "net": tr.rel_rmse(w, held, zs)}
+        errs = {"base": args.base, "net": tr.rel_rmse(w, held, zs)}
         if w0 is not None:
             errs["net_at_init"] = tr.rel_rmse(w0, held, zs)
+        if base is not None:
+            errs["learned_linear"] = tr.rel_rmse(None, held, zs)
+        tr.plan.set_taps(np.maximum(D - np.arange(D), 0) / float(D * D))
+        errs["triangle"] = tr.rel_rmse(None, held, zs)
         tr.plan.set_taps(fdkod_sinc_taps(D, 2))
         errs["sinc"] = tr.rel_rmse(None, held, zs)
-        if args.linear:
+        if args.linear and base is None:
             # the linear learned FIR (learn.py) fitted on the same training scans
             from . import learn
             h = learn.learn(R, N, P, s, D, 2, projs, zs)
@@ -296,6 +313,8 @@ def main(argv=None):
         tr.close()
     if args.out:
         np.save(args.out, w)
+        if base is not None:
+            np.save(args.out[:-4] + "_taps.npy" if args.out.endswith(".npy") else args.out + "_taps.npy", base)
     print(json.dumps({"N": N, "P": P, "s": s, "D": D, "steps": args.steps, "train_scans": args.train,
                       "held_out_scans": args.test, "train_seconds": round(t_train, 2),
                       "curve": [[int(c[0])] + [float(f"{x:.5e}") for x in c[1:]] for c in curve],

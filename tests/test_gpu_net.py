@@ -279,22 +279,26 @@ def test_net_with_taps_changed_after_setting_it(fd, oracle_mod):
 
 def test_full_size_512_net_sampled_slices(fd, oracle_mod):
     """512^3 from 720 views of 512^2, s = 3, D = 4, 40 ellipsoids + 1 % noise,
-    with the package's trained D = 4 weights (the bench's --taps net
-    configuration): full volume on the GPU, the BF16-emulating oracle on the
-    two central slices (only the detector rows they touch are decomposed)."""
+    with the package's trained D = 4 weights on top of their learned linear
+    taps (the bench's --taps net configuration): full volume on the GPU, the
+    BF16-emulating oracle with the same taps on the two central slices (only
+    the detector rows they touch are decomposed)."""
     import os
     w = phantom.WORKLOADS["fdkod_512"]
     R = 4.0 * w.N
     proj = phantom.make_projections(w)
     zs = np.array([w.N // 2 - 1, w.N // 2])   # few detector rows: a cheap oracle
-    weights = np.load(os.path.join(os.path.dirname(fd.__file__), "net_weights", "D4.npy"))
-    with fd.Plan(R, w.N, w.N, w.N, w.P, w.s, w.D) as plan:
+    wdir = os.path.join(os.path.dirname(fd.__file__), "net_weights")
+    weights = np.load(os.path.join(wdir, "D4.npy"))
+    base = np.load(os.path.join(wdir, "D4_taps.npy"))
+    assert base.shape == (2 * w.D,) and abs(base[0] + 2 * base[1:].sum() - 1.0) < 1e-9   # unit DC gain
+    with fd.Plan(R, w.N, w.N, w.N, w.P, w.s, w.D, taps=base) as plan:
         plan.set_net(weights)
         Qd = plan.filter(torch.from_numpy(proj).cuda())
         vol = plan.backproject(Qd)[torch.from_numpy(zs).cuda()].cpu().numpy().astype(np.float64)
         assert plan.device_status() == 0
         Q = Qd.cpu().numpy()                 # the filtered data both sides read
         wq = plan.net
-    want = oracle_mod.fdkod_net_slices(Q, R, w.N, w.s, w.D, wq, zs, act_round="bf16")
+    want = oracle_mod.fdkod_net_slices(Q, R, w.N, w.s, w.D, wq, zs, taps=base, act_round="bf16")
     rel = np.linalg.norm(vol - want) / np.linalg.norm(want)
     assert rel <= REL_NET, rel
