@@ -19,6 +19,7 @@ scaling); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -403,12 +404,15 @@ def slabs_main(args):
             fd.reconstruct_slabs(plan, proj, args.slabs, out)
         torch.cuda.synchronize()
         steps = max(1, min(args.steps, 5))
+        gc.collect()
+        gc.disable()  # no collector pause of this Python harness inside the host-clocked calls
         with Clocks(0) as clk:
             t0 = time.perf_counter()
             for _ in range(steps):
                 fd.reconstruct_slabs(plan, proj, args.slabs, out)
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3 / steps
+        gc.enable()
         slab_bytes = plan.info["device_bytes"] + plan.last_slab_device_bytes
         assert plan.device_status() == 0
         launches = 0
@@ -689,10 +693,13 @@ def main():
         barrier()
         torch.cuda.synchronize()
         t_calls = []
+        gc.collect()
+        gc.disable()  # no collector pause of this Python harness inside the host-clocked calls
         t_e0 = time.perf_counter()
         for _ in range(n_e2e):
             fd.reconstruct(plan, proj_h, vol_h)
             t_calls.append(time.perf_counter())
+        gc.enable()
         ms_e2e = max_over_ranks((t_calls[-1] - t_e0) * 1e3) / n_e2e
         ms_calls = np.diff([t_e0] + t_calls) * 1e3
         del vol_h
@@ -779,6 +786,7 @@ def main():
                 "slowest_call": int(np.argmax(ms_calls)),
                 "value_at_median_call": world * upd_eff / (float(np.median(ms_calls)) * 1e-3),
                 "call": "fdkod_reconstruct (C ABI, host buffers in and out, synchronous)",
+                "python_gc": "disabled during the timed calls",
                 "note": "host clock around whole calls; inside a call the upload (bands of detector rows) "
                         "overlaps the filter and the decomposition, the read-back (groups of slices) the "
                         "backprojection"},
