@@ -262,7 +262,7 @@ int fdkod_last_device_status(fdkod_plan_t *plan, uintptr_t stream);
  * this is also when the driver loads the library's device code and reserves
  * the array, which may synchronise the device, or fail with FDKOD_ERR_CUDA
  * when the device has no room left.  Make one warm-up call per device at
- * start-up, before any stream capture.
+ * start-up.
  *
  * Every call shares the array and it keeps the previous call's contents:
  * the call clears what must start at zero, but calls whose work overlaps on
