@@ -254,10 +254,14 @@ def recorded_bp_traffic(workload: str):
         return None
 
 
-def stage_rooflines(w, info, stages, qtype, peaks):
+def stage_rooflines(w, info, stages, qtype, peaks, T=None):
     """HBM fractions of the two streaming stages: algorithmic bytes (every
     input read once, every output written once) over the stage's event time,
-    against the measured copy bandwidth (fallback 6800 GB/s)."""
+    against the measured copy bandwidth (fallback 6800 GB/s).  With the
+    squares' shifted-row lengths T_q the decomposition also gets its crop
+    reads: every square reads its own T_q + 1 columns of every detector row
+    and view (sum over q of (T_q + 1) Nv P samples), most of them served from
+    L2 since neighbouring squares' crops overlap."""
     hbm = peaks.get("hbm_gbs") or 6800.0
     qb = 4 if qtype == "f32" else 2
     samples = float(w.P) * w.Nv * w.Nu
@@ -267,6 +271,12 @@ def stage_rooflines(w, info, stages, qtype, peaks):
     for name, b in (("filter", filt), ("decompose", dec)):
         ach = b / (stages[name] * 1e-3) / 1e9
         out[name] = {"bound": "hbm", "bytes": b, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm}
+    if T is not None and stages.get("decompose", 0) > 0:
+        crop = float(sum(int(t) + 1 for t in T)) * w.Nv * w.P * qb
+        ach = crop / (stages["decompose"] * 1e-3) / 1e9
+        out["decompose"].update({"crop_read_bytes": crop, "crop_read_achieved": ach, "crop_read_frac": ach / hbm,
+                                 "crop_read_note": "sum over squares of (T_q + 1) columns x Nv rows x P views "
+                                                   "read, against the same peak (mostly L2 hits)"})
     out["peak_note"] = "measured copy bandwidth" if peaks.get("hbm_gbs") else "fallback 6800 GB/s"
     return out
 
@@ -805,7 +815,8 @@ def main():
                              "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x {max_mhz:.0f} MHz"},
             "roofline_smem": {"achieved": smem_ach, "peak": smem_peak, "unit": "GB/s", "frac": smem_ach / smem_peak,
                               "bytes_per_update": SMEM_BYTES_PER_UPDATE},
-            "roofline_stages": stage_rooflines(w, info, stages, args.qtype, peaks),
+            "roofline_stages": stage_rooflines(w, info, stages, args.qtype, peaks,
+                                              plan.bounds()["T"] if w.D > 1 else None),
             **({"roofline_net": net_roofline(w, info, plan.bounds()["T"], stages, peaks), "net_weights": net_src,
                  "net_base": "triangle" if net_base is None else "learned linear taps (support 2D)"}
                if net_w is not None else {}),

@@ -89,3 +89,22 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = _run_bench(["--impl", "reference", "--workload", "fdkod_128", "--steps", "1", "--warmup", "3"],
                    {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_stage_rooflines_count_compulsory_and_crop_bytes():
+    """The streaming stages' bytes: the filter reads the projections and
+    writes Q; the decomposition reads Q once and writes S' once, and its crop
+    reads are every square's T_q + 1 columns of every row and view."""
+    import types
+    w = types.SimpleNamespace(P=8, Nv=4, Nu=16, D=2)
+    info = {"decomposed_elems": 1000}
+    T = [10, 12, 9]
+    r = bench.stage_rooflines(w, info, {"filter": 1.0, "decompose": 2.0}, "bf16", {"hbm_gbs": 1000.0}, T=T)
+    samples = 8 * 4 * 16
+    assert r["filter"]["bytes"] == samples * (4 + 2)
+    assert r["decompose"]["bytes"] == samples * 2 + 1000 * 4
+    assert r["decompose"]["crop_read_bytes"] == (11 + 13 + 10) * 4 * 8 * 2
+    assert abs(r["decompose"]["crop_read_frac"] - r["decompose"]["crop_read_bytes"] / 2e-3 / 1e9 / 1000.0) < 1e-12
+    assert r["peak_note"] == "measured copy bandwidth"
+    assert "crop_read_bytes" not in bench.stage_rooflines(w, info, {"filter": 1.0, "decompose": 2.0}, "f32", {})[
+        "decompose"]
