@@ -7,6 +7,8 @@
 // slab buffers, so slab i + 1 uploads while slab i computes and slab i - 1
 // downloads.  The filtered rows and the decomposed data are single
 // buffers: the compute stream uses them one slab at a time.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -197,9 +199,35 @@ namespace fdkod {
 // start early), then bands of Nv/4 rows.  The strided copy of a band (one
 // segment per view) keeps near the contiguous copy rate down to about
 // 256 KiB segments (measured: 211 GB/s for two bands of 512^2 x 720
-// float32, 185 for four, 127 for eight).
+// float32, 179 for four, 124 for eight).  A kernel reading a page-locked
+// host buffer moves a band at the link's rate whatever its height (207-211
+// GB/s), but its CTAs take SM slots from the compute it would overlap: it
+// moves only the two outer bands, before any compute has started.
 constexpr int kPipeChunks = 8;  // at most this many row bands
 constexpr int kPipeSlabs = 16;  // groups of slice pairs of the backprojection / read-back
+constexpr int kKernelBands = 2;  // leading bands moved by band_upload_kernel
+
+// Rows v0 .. v0 + nb - 1 of every view (view4 float4 per view, the band at
+// float4 offset off4, n4 float4 long) from a host buffer mapped into the
+// device's address space to the device copy.  Every index stays below
+// P * view4 (off4 + n4 <= view4, checked by the caller).
+__global__ void __launch_bounds__(256) band_upload_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst,
+                                                          long long view4, long long off4, int n4, int P) {
+    for (int k = blockIdx.x; k < P; k += gridDim.x) {
+        const float4 *s = src + (long long)k * view4 + off4;
+        float4 *d = dst + (long long)k * view4 + off4;
+        int j = threadIdx.x;
+        // four loads in flight per thread: the link's latency is long
+        for (; j + 3 * 256 < n4; j += 4 * 256) {
+            const float4 a = s[j], b = s[j + 256], c = s[j + 512], e = s[j + 768];
+            d[j] = a;
+            d[j + 256] = b;
+            d[j + 512] = c;
+            d[j + 768] = e;
+        }
+        for (; j < n4; j += 256) d[j] = s[j];
+    }
+}
 
 // The bands are filtered and decomposed on a stream of their own (in upload
 // order), and the groups' backprojections alternate between the caller's
@@ -212,6 +240,7 @@ struct HostPipe {
     cudaEvent_t ev_up[kPipeChunks] = {}, ev_band[kPipeChunks] = {}, ev_slab[kPipeSlabs] = {};
     cudaEvent_t ev_start = nullptr, ev_join = nullptr;
     int64_t bytes = 0;
+    int sms = 1;  // CTAs of a band upload
 };
 
 void free_host_pipe(HostPipe *hp) {
@@ -249,8 +278,11 @@ cudaError_t make_pipe(PlanImpl &p, fdkod::HostPipe **out) {
     const size_t samples = (size_t)p.g.P * p.g.Nv * p.g.Nu;
     const size_t es = p.qtype == FDKOD_F32 ? 4 : 2;
     const size_t voxels = (size_t)p.g.N * p.g.N * p.g.N;
+    int dev = 0;
     cudaError_t e;
-    if ((e = cudaMalloc(&hp->proj, sizeof(float) * samples)) != cudaSuccess ||
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&hp->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaMalloc(&hp->proj, sizeof(float) * samples)) != cudaSuccess ||
         (e = cudaMalloc(&hp->Q, es * samples)) != cudaSuccess ||
         (e = cudaMalloc(&hp->vol, sizeof(float) * voxels)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&hp->up, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -276,6 +308,40 @@ cudaError_t make_pipe(PlanImpl &p, fdkod::HostPipe **out) {
     hp->bytes = (int64_t)(sizeof(float) * samples + es * samples + sizeof(float) * voxels);
     *out = hp;
     return cudaSuccess;
+}
+
+// The device address of host buffer p of `bytes` bytes when the GPU can read
+// all of it directly -- page-locked memory mapped into the device's address
+// space (cudaHostAlloc, cudaHostRegister) whose allocation covers the whole
+// buffer, 16-byte aligned -- else nullptr (pageable memory, a buffer that
+// runs past its allocation, or a driver that does not say).
+const void *mapped_host_source(const void *p, size_t bytes) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // not sticky: clear it
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || ((uintptr_t)a.devicePointer & 15u)) return nullptr;
+    static const PFN_cuPointerGetAttribute_v4000 get = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 4000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PFN_cuPointerGetAttribute_v4000) nullptr;
+        }
+        return (PFN_cuPointerGetAttribute_v4000)fn;
+    }();
+    if (!get) return nullptr;
+    const CUdeviceptr dp = (CUdeviceptr)(uintptr_t)a.devicePointer;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS ||
+        get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS)
+        return nullptr;
+    if (dp < start || dp - start > size || bytes > size - (size_t)(dp - start)) return nullptr;
+    return a.devicePointer;
 }
 
 }  // namespace
@@ -337,11 +403,24 @@ extern "C" int fdkod_reconstruct(fdkod_plan_t *plan, const float *proj_host, flo
     }
     int order[kPipeChunks];  // outside in: 0, last, 1, last - 1, ...
     for (int i = 0, lo = 0, hi = nbands - 1; i < nbands; ++i) order[i] = (i & 1) ? hi-- : lo++;
+    // the two outer bands from a host buffer the GPU can read: a kernel (the
+    // GPU has no other work yet); every other band: strided copy-engine
+    // transfers
+    const void *mapped = (Nu % 4) == 0 ? mapped_host_source(proj_host, sizeof(float) * view * (size_t)P) : nullptr;
     const size_t pitch = sizeof(float) * view;
     for (int i = 0; i < nbands; ++i) {
         const int v0 = bv[order[i]], nb = bv[order[i] + 1] - v0;
-        SLAB_TRY(cudaMemcpy2DAsync(hp.proj + (size_t)v0 * Nu, pitch, proj_host + (size_t)v0 * Nu, pitch,
-                                   sizeof(float) * (size_t)nb * Nu, (size_t)P, cudaMemcpyHostToDevice, hp.up));
+        if (mapped && i < fdkod::kKernelBands) {
+            // float4 units: a view is Nv Nu / 4 of them, the band starts v0 Nu / 4 in
+            fdkod::band_upload_kernel<<<std::max(1, std::min(P, hp.sms)), 256, 0, hp.up>>>(
+                (const float4 *)mapped, (float4 *)hp.proj, (long long)(view / 4), (long long)v0 * Nu / 4,
+                nb * Nu / 4, P);
+            SLAB_TRY(cudaGetLastError());
+        } else {
+            SLAB_TRY(cudaMemcpy2DAsync(hp.proj + (size_t)v0 * Nu, pitch, proj_host + (size_t)v0 * Nu, pitch,
+                                       sizeof(float) * (size_t)nb * Nu, (size_t)P, cudaMemcpyHostToDevice,
+                                       hp.up));
+        }
         SLAB_TRY(cudaEventRecord(hp.ev_up[order[i]], hp.up));
     }
     SLAB_TRY(fdkod::launch_bounds(p, p.od, comp));
