@@ -307,7 +307,11 @@ int fdkod_noalloc_device_status(uintptr_t stream);
  * row-local); the volume is then backprojected in groups of slices and each
  * group is copied back while the next one is computed (an upload and a
  * read-back stream of the plan's own, ordered after the work already queued
- * on `stream`).  The volume equals fdkod_filter + fdkod_backproject bit for
+ * on `stream`).  When proj_host is page-locked memory mapped into the
+ * device's address space (cudaHostAlloc, cudaHostRegister; one allocation
+ * holding all of it, 16-byte aligned, Nu a multiple of 4), a kernel reads
+ * the two outer bands from it directly; copy-engine transfers move every
+ * other band.  The volume equals fdkod_filter + fdkod_backproject bit for
  * bit when Nv is even (for odd Nv the filter pairs rows differently: equal
  * to float32 round-off).
  * Device memory: the first call allocates, and the plan then keeps until
